@@ -1,0 +1,518 @@
+"""Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat24|rmat24_b50|rmat20|er4096]
+                    [--impl ours|reference]
+
+A step is one pass of the whole sketched path over the synthetic graph of the
+workload, starting from the CSR resident in HBM: the upper-edge index, the
+sketches of every neighbourhood, and one fused intersection pass per sketch
+(per-edge estimate, triangle-count histogram, per-vertex sums, LCC). The
+metric is sketched edge intersections per second: one (u, v) estimator
+evaluation on one sketch. The exact GPU intersection is the comparison: it is
+timed in the same run, outside the step, and gives the estimate's error.
+
+--impl reference times the CPU oracle (oracle/) on a bounded sample of the
+same workload on the host cores. Under torchrun (N > 1) every rank runs an
+independent replica of the workload (no collective on the data path); the
+time is the maximum over ranks and the value the sum of the ranks' work.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "sketched edge intersections/s"
+
+# workload -> generator + sketch configuration (BASELINE configs)
+WORKLOADS = {
+    # R-MAT scale 24, edge factor 32, Bloom at 25% of CSR bytes (b = 2), k-Hash k = 64, exact comparison
+    "rmat24": dict(gen=("rmat", 24, 32, 24), budget=0.25, b=2, khash=64, onehash=None, jaccard=False),
+    "rmat24_b50": dict(gen=("rmat", 24, 32, 24), budget=0.50, b=2, khash=64, onehash=None, jaccard=False),
+    # R-MAT scale 20, edge factor 16, Bloom at 25% (b = 2), 1-Hash k = 32, TC + LCC + per-edge Jaccard
+    "rmat20": dict(gen=("rmat", 20, 16, 20), budget=0.25, b=2, khash=None, onehash=32, jaccard=True),
+    # Erdos-Renyi n = 4096, average degree 16, Bloom 256 bits b = 2, k-Hash k = 16
+    "er4096": dict(gen=("er", 4096, 16.0, 1), bits=256, b=2, khash=16, onehash=None, jaccard=False),
+}
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def init_dist(ws, backend):
+    if ws > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group(backend=backend)
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws <= 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        torch.distributed.barrier()
+
+
+def generate(workload: str, device):
+    from paper_2208_11469_gb300 import synth
+    kind, *a = WORKLOADS[workload]["gen"]
+    if kind == "rmat":
+        scale, ef, seed = a
+        return synth.rmat(scale, ef, seed=seed, device=device)
+    n, deg, seed = a
+    return synth.erdos_renyi(n, deg, seed=seed, device=device)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        # nvidia-smi numbers GPUs physically; address this device by UUID
+        try:
+            u = str(torch.cuda.get_device_properties(index).uuid)
+            self.index = u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def budget_bits(s, n, nnz):
+    """Filter length for storage budget s of the CSR bytes (the sizing rule of
+    pg_bloom_bits_for_budget, restated for the CPU leg)."""
+    words = int(s * (4.0 * (n + 1) + 4.0 * nnz) * 8.0 / (64.0 * n)) if n > 0 else 1
+    return 64 * min(16, max(1, words))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel
+    source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h:
+        return None
+    src = os.path.join(ROOT, "paper_2208_11469_gb300", "csrc", "pg_intersect.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+# ------------------------------------------------------------- our path
+class Pipeline:
+    """Device buffers and the step of one workload."""
+
+    def __init__(self, workload: str, row_ptr, col):
+        from paper_2208_11469_gb300 import pg
+        self.pg = pg
+        cfg = WORKLOADS[workload]
+        self.cfg = cfg
+        dev = row_ptr.device
+        self.g = pg.graph(row_ptr, col, build_index=True)
+        g = self.g
+        self.n, self.nnz, self.m = g.n, g.nnz, g.m
+        bits = cfg.get("bits") or pg.bloom_bits_for_budget(cfg["budget"], g.n, g.nnz)
+        self.bits = bits
+        self.build_ws = torch.empty(max(pg.build_workspace_bytes(g), 16), dtype=torch.uint8, device=dev)
+        self.passes = []  # (name, sketch, estimator, build_fn)
+        bf = pg.alloc_sketch(g, pg.SK_BLOOM, bits=bits, b=cfg["b"], seed=1)
+        self.passes.append(("bloom", bf, pg.EST_BF_AND))
+        if cfg["khash"]:
+            self.passes.append(("khash", pg.alloc_sketch(g, pg.SK_KHASH, k=cfg["khash"], seed=1), pg.EST_KH))
+        if cfg["onehash"]:
+            self.passes.append(("onehash", pg.alloc_sketch(g, pg.SK_1HASH, k=cfg["onehash"], seed=1), pg.EST_1H))
+        self.ws = {name: pg.workspace(g, sk, est) for name, sk, est in self.passes}
+        self.out = {}
+        for name, sk, est in self.passes:
+            o = dict(tc=pg.tc_result_buffer(dev), lcc=torch.empty(g.n, dtype=torch.float32, device=dev),
+                     tri=torch.empty(g.n, dtype=torch.float64, device=dev))
+            if cfg["jaccard"]:
+                o["edge_cn"] = torch.empty(self.m, dtype=torch.float32, device=dev)
+                o["edge_jac"] = torch.empty(self.m, dtype=torch.float32, device=dev)
+            self.out[name] = o
+        self.index_events = None
+
+    def sketched_per_step(self) -> int:
+        return self.m * len(self.passes)
+
+    def step(self, ev=None):
+        """One pass of the hot path. ev: optional dict name -> (start, end) events."""
+        pg, g = self.pg, self.g
+        s = torch.cuda.current_stream()
+
+        def mark(name, i):
+            if ev is not None:
+                ev[name][i].record(s)
+
+        mark("index", 0)
+        pg.build_edge_index_into(g)
+        mark("index", 1)
+        for name, sk, est in self.passes:
+            mark("build_" + name, 0)
+            if sk.kind == pg.SK_BLOOM:
+                pg.build_bloom(g, sk.bits, sk.b, sk.seed, out=sk, workspace=self.build_ws)
+            else:
+                pg.build_minhash(g, sk.kind, sk.k, sk.seed, out=sk, workspace=self.build_ws)
+            mark("build_" + name, 1)
+        for name, sk, est in self.passes:
+            mark("pass_" + name, 0)
+            pg.analyze(g, sk, est, ws=self.ws[name], **self.out[name])
+            mark("pass_" + name, 1)
+
+    def event_names(self):
+        return ["index"] + ["build_" + p[0] for p in self.passes] + ["pass_" + p[0] for p in self.passes]
+
+    def results(self):
+        return {name: self.pg.read_tc_result(self.out[name]["tc"]) for name, _, _ in self.passes}
+
+
+def algorithmic_bytes(pipe: Pipeline, name: str) -> float:
+    """Algorithmic DRAM bytes of one fused intersection pass:
+    per undirected edge the gathered neighbour sketch row (payload bytes) plus
+    its CSR entry and the two row offsets of v (degree) for MinHash; per vertex
+    its own sketch row, its two row offsets and upper offset, and the outputs
+    (T as double, LCC as float)."""
+    sk = [p for p in pipe.passes if p[0] == name][0][1]
+    payload = sk.bits / 8 if sk.kind == pipe.pg.SK_BLOOM else 4 * sk.k
+    per_edge = payload + 4 + (8 if sk.kind != pipe.pg.SK_BLOOM else 0)
+    per_vertex = payload + 8 + 4 + 8 + 4
+    if pipe.cfg["jaccard"]:
+        per_edge += 8
+    return pipe.m * per_edge + pipe.n * per_vertex
+
+
+def time_steps(pipe: Pipeline, steps: int, warmup: int, ws: int):
+    for _ in range(warmup):
+        pipe.step()
+    torch.cuda.synchronize()
+    names = pipe.event_names()
+    evs = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+           for _ in range(steps)]
+    launches0 = pipe.pg.kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    start.record()
+    for i in range(steps):
+        pipe.step(evs[i])
+    end.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = pipe.pg.kernel_launches() - launches0
+    total_ms = start.elapsed_time(end)
+    per = {nm: float(np.mean([e[nm][0].elapsed_time(e[nm][1]) for e in evs])) for nm in names}
+    return total_ms / steps, per, launches
+
+
+def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
+    """The same step through the public API from pinned host buffers: the CSR
+    copy host->device and the results device->host are inside the timing."""
+    pg = pipe.pg
+    g = pipe.g
+    d2h = []
+    for name, _, _ in pipe.passes:
+        o = pipe.out[name]
+        d2h.append((o["lcc"], torch.empty(o["lcc"].shape, dtype=o["lcc"].dtype, pin_memory=True)))
+        d2h.append((o["tc"], torch.empty(o["tc"].shape, dtype=o["tc"].dtype, pin_memory=True)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(steps):
+        g.row_ptr.copy_(host_rp, non_blocking=True)
+        g.col.copy_(host_col, non_blocking=True)
+        pipe.step()
+        for dev_t, host_t in d2h:
+            host_t.copy_(dev_t, non_blocking=True)
+    end.record()
+    torch.cuda.synchronize()
+    wall = (time.perf_counter() - t0) * 1e3 / steps
+    h2d = host_rp.numel() * 4 + host_col.numel() * 4
+    d2h_bytes = sum(h.numel() * h.element_size() for _, h in d2h)
+    return start.elapsed_time(end) / steps, wall, h2d, d2h_bytes
+
+
+def exact_comparison(pipe: Pipeline):
+    pg, g = pipe.pg, pipe.g
+    ws = pg.workspace(g, None, pg.EST_EXACT)
+    tc = pg.tc_result_buffer(g.device)
+    pg.triangle_count(g, None, pg.EST_EXACT, ws=ws, out=tc, read=False)  # warm
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pg.triangle_count(g, None, pg.EST_EXACT, ws=ws, out=tc, read=False)
+    b.record()
+    torch.cuda.synchronize()
+    res = pg.read_tc_result(tc)
+    del ws
+    return a.elapsed_time(b), res
+
+
+# ------------------------------------------------------- CPU oracle leg
+def oracle_sample(row_ptr_d, col_d, pipe_cfg, bits, target_s=15.0, seed=0):
+    """Times the oracle on a bounded sample of the workload: a seeded random
+    set of upper edges; the oracle builds the sketches of every endpoint row
+    it needs and intersects the sampled edges, as the GPU step does for all
+    of them. Returns (rate, seconds, edges, description)."""
+    from oracle import oracle as O
+    rp = row_ptr_d.cpu().numpy().astype(np.int64)
+    n = rp.size - 1
+    gen = np.random.default_rng(seed)
+
+    def run(E):
+        # sample upper edges uniformly: draw CSR entries, keep those with v > u
+        j = gen.integers(0, rp[-1], size=4 * E + 16)
+        u = np.searchsorted(rp, j, side="right") - 1
+        v = col_d[torch.from_numpy(j).to(col_d.device)].cpu().numpy().astype(np.int64)
+        keep = v > u
+        u, v = u[keep][:E], v[keep][:E]
+        verts = np.unique(np.concatenate([u, v]))
+        # sub-CSR of the needed rows (a sketch depends only on its own row)
+        starts, ends = rp[verts], rp[verts + 1]
+        lens = ends - starts
+        sub_rp = np.zeros(verts.size + 1, np.int64)
+        sub_rp[1:] = np.cumsum(lens)
+        idx = np.repeat(starts - sub_rp[:-1], lens) + np.arange(int(sub_rp[-1]), dtype=np.int64)
+        sub_col = col_d[torch.from_numpy(idx).to(col_d.device)].cpu().numpy().astype(np.int32)
+        su = np.searchsorted(verts, u).astype(np.int32)
+        sv = np.searchsorted(verts, v).astype(np.int32)
+        sub_rp32 = sub_rp.astype(np.int32)
+        deg = lens
+        t0 = time.perf_counter()
+        bf = O.bloom_bits(sub_rp32, sub_col, bits, pipe_cfg["b"], 1)
+        c = O.bloom_pairs(bf, su, sv)
+        est = O.est_and(c, bits, pipe_cfg["b"])
+        tot = float(est.sum())
+        npass = 1
+        if pipe_cfg.get("khash"):
+            k = pipe_cfg["khash"]
+            M = O.khash(sub_rp32, sub_col, k, 1)
+            c2 = O.khash_pairs(M, su, sv)
+            tot += float(O.est_minhash(c2, np.full(c2.size, k), deg[su], deg[sv]).sum())
+            npass += 1
+        if pipe_cfg.get("onehash"):
+            k = pipe_cfg["onehash"]
+            M1 = O.onehash(sub_rp32, sub_col, k, 1)
+            cnt = O.pair_counts(sub_rp32, sub_col, O.EST_1H, M1, su, sv, seed=1)
+            tot += float(O.pair_estimates(sub_rp32, O.EST_1H, cnt, su, sv, k=k).sum())
+            npass += 1
+        dt = time.perf_counter() - t0
+        return dt, u.size, npass, verts.size, int(lens.sum())
+
+    E = 2000
+    dt, e, npass, nv, nz = run(E)
+    for _ in range(4):
+        if dt >= target_s * 0.5:
+            break
+        E = int(min(E * max(2.0, target_s / max(dt, 1e-3)), 5_000_000))
+        dt, e, npass, nv, nz = run(E)
+    desc = (f"{e} uniformly sampled upper edges ({nv} endpoint rows, {nz} CSR entries): oracle sketches of "
+            f"those rows + {npass} sketched intersections per edge, serial C/numpy on 1 host core")
+    return npass * e / dt, dt, e, desc
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    rp, cl = generate(args.workload, dev)
+    bits = cfg.get("bits") or budget_bits(cfg["budget"], rp.numel() - 1, cl.numel())
+    per_step = 4.0 * max(1, 60 // max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_sample(rp, cl, cfg, bits, target_s=min(per_step, 5.0), seed=1)
+    rates, secs, desc = [], 0.0, ""
+    for i in range(args.steps):
+        r, dt, e, desc = oracle_sample(rp, cl, cfg, bits, target_s=per_step, seed=100 + i)
+        rates.append(r)
+        secs += dt
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+            "data": "synthetic", "config": {"workload": args.workload, "bloom_bits": bits},
+            "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-exact", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    init_dist(ws, "nccl")
+    from paper_2208_11469_gb300 import build as B
+    B.build()
+    from paper_2208_11469_gb300 import pg
+
+    dev = torch.device("cuda", local)
+    rp, cl = generate(args.workload, dev)
+    pipe = Pipeline(args.workload, rp, cl)
+    torch.cuda.synchronize()
+
+    with ClockSampler(local) as clk:
+        ms, per, launches = time_steps(pipe, args.steps, args.warmup, ws)
+    ms_max = max_over_ranks(ms, ws, dev)
+    units = pipe.sketched_per_step() * ws
+    value = units / (ms_max * 1e-3)
+    res = pipe.results()
+
+    # roofline of the dominant kernel (the largest intersection pass)
+    dom = max((p[0] for p in pipe.passes), key=lambda nm: per["pass_" + nm])
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(pipe, dom)
+    achieved = alg / (per["pass_" + dom] * 1e-3) / 1e9
+    traffic = profiled_traffic(f"{dom}_pass_{args.workload}.md")
+
+    # end to end from host buffers
+    host_rp = rp.cpu().pin_memory()
+    host_col = cl.cpu().pin_memory()
+    e2e_ms, e2e_wall, h2d, d2h = e2e_steps(pipe, host_rp, host_col, args.e2e_steps)
+    e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+
+    exact = None
+    if not args.no_exact:
+        ex_ms, ex = exact_comparison(pipe)
+        rel = {nm: (r["est_tc"] - ex["exact_tc"]) / ex["exact_tc"] if ex["exact_tc"] else None
+               for nm, r in res.items()}
+        exact = {"ms": ex_ms, "exact_tc": ex["exact_tc"], "edges_per_s": pipe.m / (ex_ms * 1e-3),
+                 "tc_rel_error": rel}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, e, desc = oracle_sample(rp, cl, pipe.cfg, pipe.bits, target_s=15.0)
+        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded on-device generator)",
+            "config": {"workload": args.workload, "n": pipe.n, "nnz": pipe.nnz, "m": pipe.m,
+                       "bloom_bits": pipe.bits, "bloom_b": pipe.cfg["b"], "khash_k": pipe.cfg["khash"],
+                       "onehash_k": pipe.cfg["onehash"], "per_edge_jaccard": pipe.cfg["jaccard"],
+                       "passes": [p[0] for p in pipe.passes],
+                       "l2": "inputs larger than L2 (CSR and sketch tables >> 129 MB), no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "phases_ms": per,
+            "roofline": {"bound": "hbm", "kernel": f"k_intersect ({dom} pass, pg_analyze)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "e2e": {"value": pipe.sketched_per_step() * ws / (e2e_ms * 1e-3), "unit": "intersections/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "wall_ms_per_step": e2e_wall},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "results": res,
+            "exact_gpu": exact,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,266 @@
+/*
+ * pg.h — C ABI of the GB300-native ProbGraph hot path.
+ *
+ * Method: Besta et al., "ProbGraph: High-Performance and High-Accuracy Graph
+ * Mining with Probabilistic Set Representations", SC'22 (arXiv 2208.11469).
+ * Each vertex neighbourhood N_v gets a fixed-size sketch (Bloom filter,
+ * k-Hash MinHash or 1-Hash MinHash, Sec. II-C); |N_u ∩ N_v| is estimated
+ * per edge from the two sketches (Sec. IV) and the estimates are reduced
+ * into the triangle count (Sec. VII), per-vertex local clustering
+ * coefficients and per-edge / per-pair Jaccard and common-neighbour scores
+ * (Sec. III, Listings 3 and 6).
+ *
+ * Conventions shared by every entry point
+ *   Memory    All array arguments are DEVICE pointers owned by the caller,
+ *             unless a comment says HOST. The library allocates no device
+ *             memory; calls that need scratch take a caller-provided
+ *             workspace whose size the matching *_bytes function returns.
+ *   Streams   Every call is stream-ordered on `stream` (NULL = the legacy
+ *             default stream) and returns without synchronising it, except
+ *             pg_server_* / pg_poll, which are documented separately.
+ *   Errors    Every call returns a pg_status. Nothing is thrown across the
+ *             ABI. pg_last_error() gives a thread-local detail message.
+ *             A PG_ERR_CUDA status means a CUDA launch or runtime call
+ *             failed; the stream's work up to that call may be incomplete.
+ *   Graphs    pg_csr: int32 CSR of a simple undirected graph, both directions
+ *             of every edge stored, every row sorted ascending, no self
+ *             loops, no duplicates (Sec. II-A). nnz < 2^31. Calls trust this
+ *             unless pg_validate_csr has rejected the graph.
+ *   Edges     "Upper edges": each undirected edge once, as (u, v) with u < v
+ *             taken from row u, in CSR order (u ascending, then v
+ *             ascending). Per-edge outputs are indexed by this order
+ *             e = upper_off[u] + (position of v among row u's entries > u).
+ *   Hashing   h_i(x) = fmix32(uint32(x) XOR s_i), s_i = fmix32(seed +
+ *             i * 0x9E3779B9), where fmix32 is MurmurHash3's 32-bit
+ *             finaliser (Sec. VI-C names MurmurHash3; the seeding is this
+ *             library's choice). Bit position of h in an l-bit filter:
+ *             floor(h * l / 2^32).
+ *   Determinism  Same inputs and seed give bit-identical sketches, integer
+ *             counts and histograms. Floating totals are computed from the
+ *             integer histograms in a fixed order and are deterministic too;
+ *             per-vertex sums use double atomics (order-dependent at ~1e-16
+ *             relative).
+ */
+#ifndef PG_H
+#define PG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (the same type, declared here without CUDA headers). */
+struct CUstream_st;
+typedef struct CUstream_st *pg_stream_t;
+
+/* ------------------------------------------------------------------ status */
+typedef int32_t pg_status;
+#define PG_OK                 0
+#define PG_ERR_INVALID_ARG   (-1) /* a null/misaligned pointer, a bad size or parameter */
+#define PG_ERR_INVALID_GRAPH (-2) /* pg_validate_csr found the CSR malformed */
+#define PG_ERR_TOO_LARGE     (-3) /* a size beyond what the call supports (e.g. nnz >= 2^31) */
+#define PG_ERR_NO_MEMORY     (-4) /* workspace/arena smaller than required */
+#define PG_ERR_CUDA          (-5) /* a CUDA runtime call or kernel launch failed */
+#define PG_ERR_TIMEOUT       (-6) /* a bounded wait ran out */
+#define PG_ERR_NOT_FOUND     (-7) /* unknown ticket / handle */
+#define PG_ERR_BUSY          (-8) /* result not ready yet / queue full */
+#define PG_ERR_UNSUPPORTED   (-9) /* a parameter combination this build does not implement */
+
+/* Human-readable name of a status code (static string). */
+const char *pg_status_string(pg_status status);
+/* Detail message of the last failing call on this host thread (static per thread). */
+const char *pg_last_error(void);
+/* Library ABI version: (major << 16) | minor. */
+int32_t pg_version(void);
+/* Number of CUDA kernels this library has enqueued in this process so far
+ * (all devices and streams; a monotone counter for accounting and tests). */
+uint64_t pg_kernel_launches(void);
+
+/* ------------------------------------------------------------------- graph */
+typedef struct pg_csr {
+    const int32_t *row_ptr; /* DEVICE [n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz */
+    const int32_t *col;     /* DEVICE [nnz] neighbour ids in [0, n) */
+    int32_t n;              /* vertices, >= 0 */
+    int64_t nnz;            /* CSR entries (2 x undirected edges), 0 <= nnz < 2^31 */
+} pg_csr;
+
+/* Structural check of a CSR (Sec. II-A form): row_ptr monotone and ending at
+ * nnz, ids in range, rows strictly increasing (sorted, no duplicates), no
+ * self loops, and (if check_symmetry) every (u,v) has its (v,u).
+ * result: DEVICE int64[2]; after the stream reaches this call, result[0] is
+ * 0 if the graph is valid, else a PG_CSR_* code, and result[1] the first
+ * offending row or entry index found (any one of them if several).
+ * Returns PG_OK when the check was enqueued; the verdict is in result. */
+#define PG_CSR_OK            0
+#define PG_CSR_BAD_ROW_PTR   1
+#define PG_CSR_OUT_OF_RANGE  2
+#define PG_CSR_UNSORTED      3
+#define PG_CSR_SELF_LOOP     4
+#define PG_CSR_ASYMMETRIC    5
+pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *result,
+                          pg_stream_t stream);
+
+/* ------------------------------------------------------------ edge index */
+/* The upper-edge index: upper_off[u] = number of upper edges (u', v) with
+ * u' < u, upper_off[n] = m (undirected edges). It enumerates each edge once
+ * for the sum over E of the TC estimator (Sec. VII) and fixes the per-edge
+ * output order. Built once per graph and reused by every analysis call. */
+size_t pg_edge_index_bytes(int32_t n);
+/* index: DEVICE buffer of pg_edge_index_bytes(g->n) bytes, 16-byte aligned.
+ * Overwritten. Valid for this graph until the graph changes. */
+pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes,
+                              pg_stream_t stream);
+/* The DEVICE address of upper_off (int32 [n+1]) inside an index buffer. */
+const int32_t *pg_edge_index_upper_off(const void *index);
+
+/* ----------------------------------------------------------------- sketches */
+#define PG_SK_BLOOM 1 /* Bloom filter, Sec. II-C */
+#define PG_SK_KHASH 2 /* MinHash, k-Hash variant, Sec. II-C */
+#define PG_SK_1HASH 3 /* MinHash, 1-Hash variant, Sec. II-C */
+
+/* One sketch per vertex, row-major, row v at data + v * stride_bytes.
+ *   Bloom: bits l (multiple of 64, 64..1024) in 64-bit words, bit p of the
+ *          filter is bit (p % 64) of word p / 64; words beyond l/64 up to the
+ *          stride are zero. b hash functions h_0..h_{b-1} (1..16).
+ *   k-Hash: k uint32 (1..256): entry i = min over x in N_v of h_i(x); a
+ *          vertex with no neighbours has all entries 0xFFFFFFFF.
+ *   1-Hash: k uint32 (1..32): the min(k, d_v) smallest values of h_0 over
+ *          N_v in increasing order, then 0xFFFFFFFF padding. Because every
+ *          h_i is a bijection on 32-bit ids, storing hash values is
+ *          equivalent to storing the minimising elements of Sec. II-C. */
+typedef struct pg_sketch {
+    int32_t kind;         /* PG_SK_* */
+    uint32_t bits;        /* Bloom: l */
+    uint32_t b;           /* Bloom: hash functions per element */
+    uint32_t k;           /* MinHash: sketch size */
+    uint32_t seed;        /* hash seed */
+    int32_t n;            /* rows (must equal the graph's n) */
+    int64_t stride_bytes; /* >= row payload, multiple of 16 */
+    void *data;           /* DEVICE, n * stride_bytes, 16-byte aligned */
+} pg_sketch;
+
+/* Default row stride: the payload (l/8 or 4k bytes) rounded up to 16 bytes. */
+int64_t pg_sketch_stride(int32_t kind, uint32_t bits, uint32_t k);
+/* Filter length for a storage budget s (fraction of CSR bytes, Sec. V-A):
+ * l = 64 * floor(s * (4(n+1) + 4 nnz) * 8 / (64 n)), clamped to [64, 1024]. */
+uint32_t pg_bloom_bits_for_budget(double s, int32_t n, int64_t nnz);
+
+/* Device scratch bytes the builders need for this graph (a list of the rows
+ * too long for one warp, which are finished by a second kernel). */
+size_t pg_build_workspace_bytes(const pg_csr *g);
+
+/* Bloom filter construction (Sec. II-C): for every v, start from l zero bits
+ * and, for each x in N_v and i < b, set bit floor(h_i(x) * l / 2^32).
+ * sk: kind = PG_SK_BLOOM with bits, b, seed, n, stride_bytes, data set.
+ * workspace: DEVICE, >= pg_build_workspace_bytes(g), 16-byte aligned.
+ * Overwrites every row of sk->data. */
+pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *workspace,
+                         size_t workspace_bytes, pg_stream_t stream);
+
+/* MinHash construction (Sec. II-C), kind PG_SK_KHASH or PG_SK_1HASH, with
+ * k, seed, n, stride_bytes, data set. Overwrites the first k entries of
+ * every row of sk->data (row padding beyond k entries is not written).
+ * workspace as for pg_build_bloom. */
+pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *workspace,
+                           size_t workspace_bytes, pg_stream_t stream);
+
+/* --------------------------------------------------------------- estimators */
+#define PG_EST_EXACT       0 /* exact |N_u ∩ N_v| (no sketch) */
+#define PG_EST_BF_AND      1 /* Eq. (bf_int) on popcount(B_u AND B_v), B1 = l read as l - 1 */
+#define PG_EST_BF_L        2 /* Eq. (limit_xs): popcount(B_u AND B_v) / b */
+#define PG_EST_KH          3 /* Eq. (est_int_mh), J = #{i : min_i(u) = min_i(v)} / k */
+#define PG_EST_1H          4 /* Sec. IV-D, J = c_union / K (see pg_tc_result) */
+#define PG_EST_1H_LITERAL  5 /* Sec. IV-D as printed, J = |M1_u ∩ M1_v| / k */
+
+/* Graph-level result, written to a DEVICE pg_tc_result. */
+typedef struct pg_tc_result {
+    uint64_t edges;      /* undirected edges (or pairs) intersected */
+    uint64_t count_sum;  /* sum over them of the integer count: popcount(AND), k-Hash
+                            matches, 1-Hash c_union, or exact |N_u ∩ N_v| */
+    uint64_t exact_tc;   /* PG_EST_EXACT: the exact triangle count; else 0 */
+    uint64_t reserved;
+    double est_tc;       /* (1/3) sum over edges of the requested estimate (Sec. VII) */
+    double est_tc_alt;   /* Bloom: the other of AND / L from the same popcounts;
+                            1-Hash: the other of the c_union / literal readings; else 0 */
+} pg_tc_result;
+
+/* Number of uint64 histogram bins pg_edge_counts fills for a sketch/estimator:
+ * Bloom: l+1 (count of edges per popcount); k-Hash: 2(k+1) (edges per match
+ * count, then sum of d_u + d_v per match count); 1-Hash: 2(k+1)^2 + 2(k+1)
+ * ((c_union, K) edge counts, their degree sums, then c_lit edge counts and
+ * degree sums); exact: 0. */
+int64_t pg_hist_bins(const pg_sketch *sk, int32_t estimator);
+
+/* Workspace bytes for pg_triangle_count / pg_clustering / pg_jaccard_pairs /
+ * pg_edge_counts on this graph, sketch and estimator (sk may be NULL for
+ * PG_EST_EXACT). */
+size_t pg_workspace_bytes(const pg_csr *g, const pg_sketch *sk, int32_t estimator);
+
+/* Triangle count (Sec. VII): TC^ = (1/3) sum over undirected edges of the
+ * estimate of |N_u ∩ N_v|; with PG_EST_EXACT the exact count by degree-
+ * ordered node iteration (Sec. III, Listing 1). index: built by
+ * pg_build_edge_index for g. sk: NULL for exact. out: DEVICE pg_tc_result. */
+pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch *sk,
+                            int32_t estimator, void *workspace, size_t workspace_bytes,
+                            pg_tc_result *out, pg_stream_t stream);
+
+/* Local clustering coefficient per vertex: T_v = 1/2 sum over u in N_v of
+ * the estimate of |N_u ∩ N_v| (exact: triangles at v) and
+ * lcc_v = 2 T_v / (d_v (d_v - 1)), 0 when d_v < 2; not clamped to 1.
+ * lcc: DEVICE float [n]; tri: DEVICE double [n] or NULL; tc: DEVICE
+ * pg_tc_result or NULL (the triangle count comes from the same pass). */
+pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk,
+                        int32_t estimator, void *workspace, size_t workspace_bytes,
+                        float *lcc, double *tri, pg_tc_result *tc, pg_stream_t stream);
+
+/* Common neighbours and Jaccard (Listings 3 and 6): cn = estimate of
+ * |N_u ∩ N_v| (not clamped); jac = I / (d_u + d_v - I) with
+ * I = clamp(cn, 0, min(d_u, d_v)), 0 when d_u + d_v = 0.
+ * pairs: DEVICE int32 [2P] as (u0, v0, u1, v1, ...), any vertices in [0, n);
+ * or NULL for every upper edge (then P is ignored and outputs have m entries
+ * in upper-edge order). cn, jac: DEVICE float, either may be NULL. */
+pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *sk,
+                           int32_t estimator, const int32_t *pairs, int64_t P,
+                           void *workspace, size_t workspace_bytes, float *cn, float *jac,
+                           pg_stream_t stream);
+
+/* The integer counts behind every estimate, for checking and analysis:
+ * count: DEVICE int32 [m or P] or NULL — popcount(AND) / k-Hash matches /
+ * 1-Hash c_union / exact |N_u ∩ N_v|; aux: DEVICE int32 [m or P] or NULL —
+ * 1-Hash only: K | (c_lit << 16); hist: DEVICE uint64 [pg_hist_bins] or NULL.
+ * pairs as in pg_jaccard_pairs. */
+pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk,
+                         int32_t estimator, const int32_t *pairs, int64_t P,
+                         void *workspace, size_t workspace_bytes, int32_t *count,
+                         int32_t *aux, uint64_t *hist, pg_stream_t stream);
+
+/* Everything the hot path produces, in ONE pass over the upper edges
+ * (sketch intersection, estimate, TC histogram, per-vertex sums, per-edge
+ * scores). Every pointer is DEVICE and optional (NULL = not wanted):
+ *   tc         pg_tc_result, as pg_triangle_count
+ *   lcc, tri   float [n], double [n], as pg_clustering
+ *   edge_cn, edge_jac    float [m], as pg_jaccard_pairs over all upper edges
+ *   edge_count, edge_aux int32 [m], as pg_edge_counts (edge_aux: 1-Hash only)
+ *   hist       uint64 [pg_hist_bins], as pg_edge_counts
+ * With PG_EST_EXACT the per-edge outputs take a second kernel over full rows
+ * and edge_aux / hist are not written. */
+typedef struct pg_outputs {
+    pg_tc_result *tc;
+    float *lcc;
+    double *tri;
+    float *edge_cn;
+    float *edge_jac;
+    int32_t *edge_count;
+    int32_t *edge_aux;
+    uint64_t *hist;
+} pg_outputs;
+pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                     void *workspace, size_t workspace_bytes, const pg_outputs *out,
+                     pg_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PG_H */

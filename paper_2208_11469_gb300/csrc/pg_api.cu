@@ -1,0 +1,482 @@
+// The C ABI of include/pg.h: argument checks, workspace carving, launches.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "pg_internal.cuh"
+
+namespace pg {
+
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+void note_launch(int count) { g_launches.fetch_add((uint64_t)count, std::memory_order_relaxed); }
+
+pg_status set_error(pg_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pg_status cuda_status(cudaError_t e, const char *what) {
+    snprintf(g_err, sizeof(g_err), "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    return PG_ERR_CUDA;
+}
+
+const DeviceInfo &device_info() {
+    static std::mutex mu;
+    static DeviceInfo cache[64];
+    static bool have[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!have[dev]) {
+        int sms = 0, thr = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&thr, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+        cache[dev].sm_count = sms > 0 ? sms : 1;
+        cache[dev].max_threads_per_sm = thr > 0 ? thr : 2048;
+        have[dev] = true;
+    }
+    return cache[dev];
+}
+
+namespace {
+
+pg_status check_graph(const pg_csr *g) {
+    PG_REQUIRE(g != nullptr, PG_ERR_INVALID_ARG, "graph is NULL");
+    PG_REQUIRE(g->n >= 0, PG_ERR_INVALID_ARG, "n = %d is negative", g->n);
+    PG_REQUIRE(g->nnz >= 0, PG_ERR_INVALID_ARG, "nnz = %lld is negative", (long long)g->nnz);
+    PG_REQUIRE(g->nnz < (int64_t(1) << 31), PG_ERR_TOO_LARGE, "nnz = %lld does not fit int32 CSR",
+               (long long)g->nnz);
+    PG_REQUIRE(g->row_ptr != nullptr, PG_ERR_INVALID_ARG, "row_ptr is NULL");
+    PG_REQUIRE(g->nnz == 0 || g->col != nullptr, PG_ERR_INVALID_ARG, "col is NULL");
+    PG_REQUIRE((reinterpret_cast<uintptr_t>(g->row_ptr) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(g->col) & 3u) == 0,
+               PG_ERR_INVALID_ARG, "row_ptr/col must be 4-byte aligned");
+    return PG_OK;
+}
+
+int64_t payload_bytes(const pg_sketch *sk) {
+    return sk->kind == PG_SK_BLOOM ? (int64_t)sk->bits / 8 : 4 * (int64_t)sk->k;
+}
+
+pg_status check_sketch(const pg_csr *g, const pg_sketch *sk) {
+    PG_REQUIRE(sk != nullptr, PG_ERR_INVALID_ARG, "sketch is NULL");
+    PG_REQUIRE(sk->kind == PG_SK_BLOOM || sk->kind == PG_SK_KHASH || sk->kind == PG_SK_1HASH,
+               PG_ERR_INVALID_ARG, "unknown sketch kind %d", sk->kind);
+    PG_REQUIRE(sk->n == g->n, PG_ERR_INVALID_ARG, "sketch has %d rows, graph %d vertices", sk->n, g->n);
+    if (sk->kind == PG_SK_BLOOM) {
+        PG_REQUIRE(sk->bits >= 64 && sk->bits % 64 == 0, PG_ERR_INVALID_ARG,
+                   "Bloom bits = %u must be a positive multiple of 64", sk->bits);
+        PG_REQUIRE(sk->bits <= 1024, PG_ERR_UNSUPPORTED, "Bloom bits = %u > 1024", sk->bits);
+        PG_REQUIRE(sk->b >= 1 && sk->b <= 16, PG_ERR_INVALID_ARG, "Bloom b = %u not in [1, 16]", sk->b);
+    } else if (sk->kind == PG_SK_KHASH) {
+        PG_REQUIRE(sk->k >= 1, PG_ERR_INVALID_ARG, "k must be >= 1");
+        PG_REQUIRE(sk->k <= 256, PG_ERR_UNSUPPORTED, "k-Hash k = %u > 256", sk->k);
+    } else {
+        PG_REQUIRE(sk->k >= 1, PG_ERR_INVALID_ARG, "k must be >= 1");
+        PG_REQUIRE(sk->k <= 32, PG_ERR_UNSUPPORTED, "1-Hash k = %u > 32", sk->k);
+    }
+    PG_REQUIRE(sk->stride_bytes % 16 == 0 && sk->stride_bytes >= payload_bytes(sk),
+               PG_ERR_INVALID_ARG, "stride %lld must be a multiple of 16 and >= %lld",
+               (long long)sk->stride_bytes, (long long)payload_bytes(sk));
+    PG_REQUIRE(sk->stride_bytes <= 1024, PG_ERR_UNSUPPORTED, "stride %lld > 1024",
+               (long long)sk->stride_bytes);
+    PG_REQUIRE(g->n == 0 || sk->data != nullptr, PG_ERR_INVALID_ARG, "sketch data is NULL");
+    PG_REQUIRE(aligned16(sk->data), PG_ERR_INVALID_ARG, "sketch data must be 16-byte aligned");
+    return PG_OK;
+}
+
+pg_status check_estimator(const pg_sketch *sk, int32_t est) {
+    switch (est) {
+        case PG_EST_EXACT: return PG_OK;
+        case PG_EST_BF_AND:
+        case PG_EST_BF_L:
+            PG_REQUIRE(sk && sk->kind == PG_SK_BLOOM, PG_ERR_INVALID_ARG,
+                       "estimator %d needs a Bloom sketch", est);
+            return PG_OK;
+        case PG_EST_KH:
+            PG_REQUIRE(sk && sk->kind == PG_SK_KHASH, PG_ERR_INVALID_ARG,
+                       "estimator %d needs a k-Hash sketch", est);
+            return PG_OK;
+        case PG_EST_1H:
+        case PG_EST_1H_LITERAL:
+            PG_REQUIRE(sk && sk->kind == PG_SK_1HASH, PG_ERR_INVALID_ARG,
+                       "estimator %d needs a 1-Hash sketch", est);
+            return PG_OK;
+        default: return set_error(PG_ERR_INVALID_ARG, "unknown estimator %d", est);
+    }
+}
+
+// Workspace layout of the analysis calls:
+//   [estimator table][histogram][S: n doubles][exact path scratch]
+struct Workspace {
+    double *table;
+    uint64_t *hist;
+    double *S;
+    void *exact;
+    size_t total;
+};
+
+Workspace carve(const pg_csr *g, const pg_sketch *sk, int32_t est, void *base) {
+    Workspace w{};
+    uint8_t *p = static_cast<uint8_t *>(base);
+    size_t off = 0;
+    if (est != PG_EST_EXACT && sk) {
+        w.table = reinterpret_cast<double *>(p + off);
+        off += intersect_table_bytes(sk->kind, sk->bits, sk->k);
+        w.hist = reinterpret_cast<uint64_t *>(p + off);
+        off += round_up(8 * (size_t)hist_bins(sk->kind, sk->bits, sk->k), 256);
+    }
+    w.S = reinterpret_cast<double *>(p + off);
+    off += round_up(8 * (size_t)g->n + 8, 256);
+    if (est == PG_EST_EXACT) {
+        w.exact = p + off;
+        off += exact_workspace_bytes(g->n, g->nnz);
+    }
+    w.total = off;
+    return w;
+}
+
+pg_status common_checks(const pg_csr *g, const void *index, bool need_index, const pg_sketch *sk,
+                        int32_t est, void *ws, size_t ws_bytes, Workspace *w) {
+    pg_status st = check_graph(g);
+    if (st) return st;
+    st = check_estimator(sk, est);
+    if (st) return st;
+    if (est != PG_EST_EXACT) {
+        st = check_sketch(g, sk);
+        if (st) return st;
+    }
+    PG_REQUIRE(!need_index || index != nullptr, PG_ERR_INVALID_ARG, "edge index is NULL");
+    PG_REQUIRE(index == nullptr || aligned16(index), PG_ERR_INVALID_ARG,
+               "edge index must be 16-byte aligned");
+    *w = carve(g, est == PG_EST_EXACT ? nullptr : sk, est, ws);
+    PG_REQUIRE(ws != nullptr || w->total == 0, PG_ERR_INVALID_ARG, "workspace is NULL");
+    PG_REQUIRE(aligned16(ws), PG_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
+    PG_REQUIRE(ws_bytes >= w->total, PG_ERR_NO_MEMORY, "workspace has %zu bytes, needs %zu",
+               ws_bytes, w->total);
+    return PG_OK;
+}
+
+}  // namespace
+}  // namespace pg
+
+using namespace pg;
+
+extern "C" {
+
+const char *pg_status_string(pg_status s) {
+    switch (s) {
+        case PG_OK: return "PG_OK";
+        case PG_ERR_INVALID_ARG: return "PG_ERR_INVALID_ARG";
+        case PG_ERR_INVALID_GRAPH: return "PG_ERR_INVALID_GRAPH";
+        case PG_ERR_TOO_LARGE: return "PG_ERR_TOO_LARGE";
+        case PG_ERR_NO_MEMORY: return "PG_ERR_NO_MEMORY";
+        case PG_ERR_CUDA: return "PG_ERR_CUDA";
+        case PG_ERR_TIMEOUT: return "PG_ERR_TIMEOUT";
+        case PG_ERR_NOT_FOUND: return "PG_ERR_NOT_FOUND";
+        case PG_ERR_BUSY: return "PG_ERR_BUSY";
+        case PG_ERR_UNSUPPORTED: return "PG_ERR_UNSUPPORTED";
+        default: return "PG_ERR_UNKNOWN";
+    }
+}
+
+const char *pg_last_error(void) { return g_err; }
+
+int32_t pg_version(void) { return (1 << 16) | 0; }
+
+uint64_t pg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *result,
+                          pg_stream_t stream) {
+    pg_status st = check_graph(g);
+    if (st) return st;
+    PG_REQUIRE(result != nullptr && (reinterpret_cast<uintptr_t>(result) & 7u) == 0,
+               PG_ERR_INVALID_ARG, "result must be an 8-byte aligned device int64[2]");
+    PG_TRY_CUDA(launch_validate(g->row_ptr, g->col, g->n, g->nnz, check_symmetry, result, stream),
+                "pg_validate_csr");
+    return PG_OK;
+}
+
+size_t pg_edge_index_bytes(int32_t n) { return n < 0 ? 0 : upper_index_bytes(n); }
+
+const int32_t *pg_edge_index_upper_off(const void *index) {
+    return static_cast<const int32_t *>(index);
+}
+
+pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes, pg_stream_t stream) {
+    pg_status st = check_graph(g);
+    if (st) return st;
+    PG_REQUIRE(index != nullptr && aligned16(index), PG_ERR_INVALID_ARG,
+               "index must be a 16-byte aligned device buffer");
+    PG_REQUIRE(index_bytes >= upper_index_bytes(g->n), PG_ERR_NO_MEMORY,
+               "index has %zu bytes, needs %zu", index_bytes, upper_index_bytes(g->n));
+    int32_t *upper_off = static_cast<int32_t *>(index);
+    int32_t *scratch = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(index) +
+                                                   round_up(4 * ((size_t)g->n + 1), 256));
+    PG_TRY_CUDA(launch_upper_index(g->row_ptr, g->col, g->n, upper_off, scratch, stream),
+                "pg_build_edge_index");
+    return PG_OK;
+}
+
+int64_t pg_sketch_stride(int32_t kind, uint32_t bits, uint32_t k) {
+    int64_t payload = kind == PG_SK_BLOOM ? (int64_t)bits / 8 : 4 * (int64_t)k;
+    return (int64_t)round_up((size_t)(payload > 0 ? payload : 16), 16);
+}
+
+uint32_t pg_bloom_bits_for_budget(double s, int32_t n, int64_t nnz) {
+    if (n <= 0 || !(s > 0.0)) return 64;
+    const double csr_bytes = 4.0 * ((double)n + 1.0) + 4.0 * (double)nnz;
+    double words = s * csr_bytes * 8.0 / (64.0 * (double)n);
+    int64_t w = (int64_t)words;
+    if (w < 1) w = 1;
+    if (w > 16) w = 16;
+    return (uint32_t)(64 * w);
+}
+
+size_t pg_build_workspace_bytes(const pg_csr *g) {
+    if (!g || g->nnz < 0) return 0;
+    return build_workspace_bytes(g->nnz);
+}
+
+static pg_status build_common(const pg_csr *g, const pg_sketch *sk, void *ws, size_t ws_bytes) {
+    pg_status st = check_graph(g);
+    if (st) return st;
+    st = check_sketch(g, sk);
+    if (st) return st;
+    PG_REQUIRE(ws != nullptr && aligned16(ws), PG_ERR_INVALID_ARG,
+               "build workspace must be a 16-byte aligned device buffer");
+    PG_REQUIRE(ws_bytes >= build_workspace_bytes(g->nnz), PG_ERR_NO_MEMORY,
+               "build workspace has %zu bytes, needs %zu", ws_bytes,
+               build_workspace_bytes(g->nnz));
+    return PG_OK;
+}
+
+pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *ws, size_t ws_bytes,
+                         pg_stream_t stream) {
+    pg_status st = build_common(g, sk, ws, ws_bytes);
+    if (st) return st;
+    PG_REQUIRE(sk->kind == PG_SK_BLOOM, PG_ERR_INVALID_ARG, "pg_build_bloom needs kind PG_SK_BLOOM");
+    PG_TRY_CUDA(launch_build_bloom(g->row_ptr, g->col, g->n, sk->bits, sk->b, sk->seed,
+                                   static_cast<uint8_t *>(sk->data), sk->stride_bytes,
+                                   static_cast<int32_t *>(ws), stream),
+                "pg_build_bloom");
+    return PG_OK;
+}
+
+pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *ws, size_t ws_bytes,
+                           pg_stream_t stream) {
+    pg_status st = build_common(g, sk, ws, ws_bytes);
+    if (st) return st;
+    if (sk->kind == PG_SK_KHASH) {
+        PG_TRY_CUDA(launch_build_khash(g->row_ptr, g->col, g->n, sk->k, sk->seed,
+                                       static_cast<uint8_t *>(sk->data), sk->stride_bytes,
+                                       static_cast<int32_t *>(ws), stream),
+                    "pg_build_minhash");
+    } else if (sk->kind == PG_SK_1HASH) {
+        PG_TRY_CUDA(launch_build_1hash(g->row_ptr, g->col, g->n, sk->k, sk->seed,
+                                       static_cast<uint8_t *>(sk->data), sk->stride_bytes,
+                                       static_cast<int32_t *>(ws), stream),
+                    "pg_build_minhash");
+    } else {
+        return set_error(PG_ERR_INVALID_ARG, "pg_build_minhash needs kind PG_SK_KHASH or PG_SK_1HASH");
+    }
+    return PG_OK;
+}
+
+int64_t pg_hist_bins(const pg_sketch *sk, int32_t estimator) {
+    if (!sk || estimator == PG_EST_EXACT) return 0;
+    return hist_bins(sk->kind, sk->bits, sk->k);
+}
+
+size_t pg_workspace_bytes(const pg_csr *g, const pg_sketch *sk, int32_t estimator) {
+    if (!g || g->n < 0 || g->nnz < 0) return 0;
+    if (estimator != PG_EST_EXACT && !sk) return 0;
+    return carve(g, estimator == PG_EST_EXACT ? nullptr : sk, estimator, nullptr).total;
+}
+
+pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch *sk,
+                            int32_t estimator, void *ws, size_t ws_bytes, pg_tc_result *out,
+                            pg_stream_t stream) {
+    Workspace w;
+    pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
+    if (st) return st;
+    PG_REQUIRE(out != nullptr && (reinterpret_cast<uintptr_t>(out) & 7u) == 0, PG_ERR_INVALID_ARG,
+               "out must be an 8-byte aligned device pg_tc_result");
+    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    if (estimator == PG_EST_EXACT) {
+        PG_TRY_CUDA(launch_exact_tc(g->row_ptr, g->col, g->n, g->nnz, upper_off, w.exact, nullptr,
+                                    out, stream),
+                    "pg_triangle_count(exact)");
+        return PG_OK;
+    }
+    const size_t bins = (size_t)hist_bins(sk->kind, sk->bits, sk->k);
+    launch_fill_u64(w.hist, bins, 0, stream);
+    EdgeOutputs eo{};
+    eo.hist = w.hist;
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+                                    estimator, eo, w.table, stream),
+                "pg_triangle_count");
+    PG_TRY_CUDA(launch_tc_finalize(w.hist, *sk, estimator, out, stream), "pg_triangle_count");
+    return PG_OK;
+}
+
+pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                        void *ws, size_t ws_bytes, float *lcc, double *tri, pg_tc_result *tc,
+                        pg_stream_t stream) {
+    Workspace w;
+    pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
+    if (st) return st;
+    PG_REQUIRE(g->n == 0 || lcc != nullptr || tri != nullptr, PG_ERR_INVALID_ARG,
+               "lcc and tri are both NULL");
+    PG_REQUIRE((reinterpret_cast<uintptr_t>(tri) & 7u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(tc) & 7u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(lcc) & 3u) == 0,
+               PG_ERR_INVALID_ARG, "misaligned output pointer");
+    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    double *S = tri ? tri : w.S;
+    launch_fill_f64(S, (size_t)g->n, 0.0, stream);
+    if (estimator == PG_EST_EXACT) {
+        PG_TRY_CUDA(launch_exact_tc(g->row_ptr, g->col, g->n, g->nnz, upper_off, w.exact, S, tc,
+                                    stream),
+                    "pg_clustering(exact)");
+    } else {
+        EdgeOutputs eo{};
+        eo.S = S;
+        if (tc) {
+            eo.hist = w.hist;
+            launch_fill_u64(w.hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+        }
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+                                        estimator, eo, w.table, stream),
+                    "pg_clustering");
+        if (tc) PG_TRY_CUDA(launch_tc_finalize(w.hist, *sk, estimator, tc, stream), "pg_clustering");
+    }
+    PG_TRY_CUDA(launch_lcc_finalize(g->row_ptr, g->n, S, lcc, tri, stream), "pg_clustering");
+    return PG_OK;
+}
+
+static pg_status pairs_common(const pg_csr *g, const void *index, const pg_sketch *sk,
+                              int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
+                              size_t ws_bytes, Workspace *w) {
+    pg_status st = common_checks(g, index, pairs == nullptr, sk, estimator, ws, ws_bytes, w);
+    if (st) return st;
+    if (pairs) {
+        PG_REQUIRE(P >= 0, PG_ERR_INVALID_ARG, "P = %lld is negative", (long long)P);
+        PG_REQUIRE((reinterpret_cast<uintptr_t>(pairs) & 7u) == 0, PG_ERR_INVALID_ARG,
+                   "pairs must be 8-byte aligned");
+    }
+    return PG_OK;
+}
+
+pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *sk,
+                           int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
+                           size_t ws_bytes, float *cn, float *jac, pg_stream_t stream) {
+    Workspace w;
+    pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
+    if (st) return st;
+    EdgeOutputs eo{};
+    eo.cn = cn;
+    eo.jac = jac;
+    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    if (estimator == PG_EST_EXACT) {
+        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, pairs, P, eo, stream),
+                    "pg_jaccard_pairs(exact)");
+    } else {
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, pairs, P, *sk,
+                                        estimator, eo, w.table, stream),
+                    "pg_jaccard_pairs");
+    }
+    return PG_OK;
+}
+
+pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk,
+                         int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
+                         size_t ws_bytes, int32_t *count, int32_t *aux, uint64_t *hist,
+                         pg_stream_t stream) {
+    Workspace w;
+    pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
+    if (st) return st;
+    EdgeOutputs eo{};
+    eo.count = count;
+    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    if (estimator == PG_EST_EXACT) {
+        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, pairs, P, eo, stream),
+                    "pg_edge_counts(exact)");
+        return PG_OK;
+    }
+    eo.aux = aux;
+    if (hist) {
+        PG_REQUIRE((reinterpret_cast<uintptr_t>(hist) & 7u) == 0, PG_ERR_INVALID_ARG,
+                   "hist must be 8-byte aligned");
+        eo.hist = hist;
+        launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+    }
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, pairs, P, *sk, estimator,
+                                    eo, w.table, stream),
+                "pg_edge_counts");
+    return PG_OK;
+}
+
+pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                     void *ws, size_t ws_bytes, const pg_outputs *out, pg_stream_t stream) {
+    Workspace w;
+    pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
+    if (st) return st;
+    PG_REQUIRE(out != nullptr, PG_ERR_INVALID_ARG, "outputs is NULL");
+    PG_REQUIRE((reinterpret_cast<uintptr_t>(out->tri) & 7u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->tc) & 7u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->hist) & 7u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->lcc) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_cn) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_jac) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_count) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_aux) & 3u) == 0,
+               PG_ERR_INVALID_ARG, "misaligned output pointer");
+    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const bool want_vertex = out->lcc || out->tri;
+    double *S = want_vertex ? (out->tri ? out->tri : w.S) : nullptr;
+    if (S) launch_fill_f64(S, (size_t)g->n, 0.0, stream);
+    if (estimator == PG_EST_EXACT) {
+        if (S || out->tc)
+            PG_TRY_CUDA(launch_exact_tc(g->row_ptr, g->col, g->n, g->nnz, upper_off, w.exact, S,
+                                        out->tc, stream),
+                        "pg_analyze(exact)");
+        if (out->edge_cn || out->edge_jac || out->edge_count) {
+            EdgeOutputs eo{};
+            eo.cn = out->edge_cn;
+            eo.jac = out->edge_jac;
+            eo.count = out->edge_count;
+            PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, eo,
+                                           stream),
+                        "pg_analyze(exact)");
+        }
+    } else {
+        EdgeOutputs eo{};
+        eo.S = S;
+        eo.cn = out->edge_cn;
+        eo.jac = out->edge_jac;
+        eo.count = out->edge_count;
+        eo.aux = out->edge_aux;
+        uint64_t *hist = out->hist ? out->hist : (out->tc ? w.hist : nullptr);
+        if (hist) {
+            eo.hist = hist;
+            launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+        }
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+                                        estimator, eo, w.table, stream),
+                    "pg_analyze");
+        if (out->tc) PG_TRY_CUDA(launch_tc_finalize(hist, *sk, estimator, out->tc, stream), "pg_analyze");
+    }
+    if (S) PG_TRY_CUDA(launch_lcc_finalize(g->row_ptr, g->n, S, out->lcc, out->tri, stream), "pg_analyze");
+    return PG_OK;
+}
+
+}  // extern "C"

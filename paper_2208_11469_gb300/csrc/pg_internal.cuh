@@ -1,0 +1,133 @@
+// Internal declarations shared by the CUDA translation units of libpg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pg.h"
+
+namespace pg {
+
+// ------------------------------------------------------------ error helpers
+pg_status set_error(pg_status st, const char *fmt, ...);
+pg_status cuda_status(cudaError_t e, const char *what);
+#define PG_TRY_CUDA(expr, what)                                                   \
+    do {                                                                          \
+        cudaError_t _e = (expr);                                                  \
+        if (_e != cudaSuccess) return ::pg::cuda_status(_e, what);                \
+    } while (0)
+#define PG_CHECK_LAUNCH(what) PG_TRY_CUDA(cudaGetLastError(), what)
+#define PG_REQUIRE(cond, st, ...)                                                 \
+    do {                                                                          \
+        if (!(cond)) return ::pg::set_error(st, __VA_ARGS__);                     \
+    } while (0)
+
+struct DeviceInfo {
+    int sm_count;
+    int max_threads_per_sm;
+};
+const DeviceInfo &device_info();
+
+// Process-wide count of kernels this library has enqueued (pg_kernel_launches).
+void note_launch(int count = 1);
+
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ------------------------------------------------------- device primitives
+// MurmurHash3's 32-bit finaliser (two multiply / xor-shift rounds).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+// Seed of hash function i.
+__device__ __forceinline__ uint32_t hash_seed(uint32_t seed, uint32_t i) {
+    return fmix32(seed + i * 0x9E3779B9u);
+}
+// The first xor-shift round of fmix32 is linear over XOR, so
+// fmix32(x ^ s) = tail(pre(x) ^ pre(s)) with pre(y) = y ^ (y >> 16).
+// Hoisting pre(x) out of a loop over hash functions saves two operations
+// per hash without changing any value.
+__device__ __forceinline__ uint32_t fmix_pre(uint32_t y) { return y ^ (y >> 16); }
+__device__ __forceinline__ uint32_t fmix_tail(uint32_t h) {
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+// h_i(x) given pre(s_i).
+__device__ __forceinline__ uint32_t hash_pre(uint32_t pre_x, uint32_t pre_s) {
+    return fmix_tail(pre_x ^ pre_s);
+}
+// Position of hash h in an l-bit filter: floor(h * l / 2^32).
+__device__ __forceinline__ uint32_t bit_pos(uint32_t h, uint32_t l) { return __umulhi(h, l); }
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// ------------------------------------------------------------ launchers
+// Defined in pg_index.cu
+void launch_fill_u64(uint64_t *p, size_t count, uint64_t value, cudaStream_t s);
+void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s);
+size_t upper_index_bytes(int32_t n);
+size_t scan_scratch_bytes(int64_t count);
+// In-place exclusive prefix sum of count int32 values (scratch: scan_scratch_bytes).
+cudaError_t launch_exclusive_scan(int32_t *data, int64_t count, int32_t *scratch, cudaStream_t s);
+cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                               int32_t *upper_off, int32_t *scratch, cudaStream_t s);
+cudaError_t launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                            int check_symmetry, int64_t *result, cudaStream_t s);
+
+// Defined in pg_sketch.cu. hub_base: build workspace (build_workspace_bytes).
+size_t build_workspace_bytes(int64_t nnz);
+cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                               uint32_t l, uint32_t b, uint32_t seed, uint8_t *data,
+                               int64_t stride, int32_t *hub_base, cudaStream_t s);
+cudaError_t launch_build_khash(const int32_t *row_ptr, const int32_t *col, int32_t n, uint32_t k,
+                               uint32_t seed, uint8_t *data, int64_t stride, int32_t *hub_base,
+                               cudaStream_t s);
+cudaError_t launch_build_1hash(const int32_t *row_ptr, const int32_t *col, int32_t n, uint32_t k,
+                               uint32_t seed, uint8_t *data, int64_t stride, int32_t *hub_base,
+                               cudaStream_t s);
+
+// Defined in pg_intersect.cu
+struct EdgeOutputs {
+    double *S;          // [n] sum over incident edges of the estimate (zeroed by caller) or null
+    float *cn;          // per edge/pair
+    float *jac;         // per edge/pair
+    int32_t *count;     // per edge/pair
+    int32_t *aux;       // per edge/pair (1-Hash)
+    uint64_t *hist;     // [bins] (zeroed by caller) or null
+};
+int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k);
+size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k);
+// Enqueue the estimator-table kernel (into table_ws) and the intersection
+// kernel over every upper edge (pairs == nullptr) or over P pairs.
+cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                                const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                                const pg_sketch &sk, int32_t estimator, const EdgeOutputs &out,
+                                double *table_ws, cudaStream_t s);
+cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,
+                               pg_tc_result *out, cudaStream_t s);
+cudaError_t launch_lcc_finalize(const int32_t *row_ptr, int32_t n, double *S, float *lcc,
+                                double *tri, cudaStream_t s);
+
+// Defined in pg_exact.cu
+size_t exact_workspace_bytes(int32_t n, int64_t nnz);
+// Exact triangle count and per-vertex S_v = 2 * (triangles at v) by
+// degree-ordered node iteration. S: DEVICE double [n] zeroed by the caller,
+// or null. tc: DEVICE pg_tc_result or null.
+cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                            const int32_t *upper_off, void *ws, double *S, pg_tc_result *tc,
+                            cudaStream_t s);
+// Exact |N_u ∩ N_v| per upper edge (pairs == nullptr) or per pair, into
+// out.count / out.cn / out.jac.
+cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                               const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                               const EdgeOutputs &out, cudaStream_t s);
+
+}  // namespace pg

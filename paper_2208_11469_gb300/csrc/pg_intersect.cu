@@ -1,0 +1,524 @@
+// Sketch intersection, per-edge estimation and reduction (Sec. IV, Sec. VII).
+//
+// One kernel serves all three sketch kinds and both work sources:
+//   - every upper edge (u < v) of the graph, enumerated from the upper-edge
+//     index, or
+//   - an explicit list of vertex pairs.
+// A "group" of L lanes handles one edge at a time; each lane loads 16-byte
+// vectors of the two sketch rows (the row of u repeats along a CSR row and
+// is served from L1), the group reduces its partial count with shuffles and
+// the epilogue turns the integer count into the estimate:
+//   Bloom : B1 = popcount(B_u AND B_v)          -> Eq. (bf_int) / Eq. (limit_xs)
+//   k-Hash: c = #{i : min_i(u) = min_i(v)}        -> Eq. (est_int_mh)
+//   1-Hash: c_union, K, c_lit (warp-wide merge)   -> Sec. IV-D
+// Graph totals come from exact integer histograms of the counts (block-local
+// in shared memory, merged with integer atomics) and one fixed-order double
+// dot product in k_tc_finalize, so they are deterministic. Per-vertex sums
+// S_v = sum over incident edges of the estimate use double atomics.
+//
+// Edge partition: the m upper edges are split into Q equal contiguous ranges,
+// one per group (a persistent grid of Q groups); each group binary-searches
+// its first vertex once and then walks the index.
+#include "pg_internal.cuh"
+
+namespace pg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBatch = 4;      // edges a group has in flight
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+enum Kind { BLOOM = PG_SK_BLOOM, KHASH = PG_SK_KHASH, ONEHASH = PG_SK_1HASH };
+
+struct Params {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    int32_t n;
+    const int32_t *upper_off;
+    const int32_t *pairs;
+    int64_t P;
+    const uint8_t *data;
+    int64_t stride;
+    int32_t nvec;       // 16-byte vectors per row that carry payload
+    uint32_t l;         // Bloom bits
+    uint32_t k;         // MinHash k
+    int32_t est;
+    int32_t need_deg;   // per-edge degrees needed
+    int32_t need_est;   // per-edge estimate needed (S, cn or jac)
+    const double *table;  // estimator table in global memory
+    int32_t table_len;
+    // outputs
+    double *S;
+    float *cn;
+    float *jac;
+    int32_t *count;
+    int32_t *aux;
+    uint64_t *hist;
+    int32_t hist_len;   // number of uint64 bins
+};
+
+__device__ __forceinline__ uint4 ldg4(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Per-lane partial count of one edge for Bloom / k-Hash.
+template <int KIND, int L>
+__device__ __forceinline__ uint32_t lane_count(const Params &p, const uint8_t *ru, const uint8_t *rv,
+                                               unsigned g) {
+    uint32_t c = 0;
+    for (int q = (int)g; q < p.nvec; q += L) {
+        const uint4 a = ldg4(ru + 16 * q), b = ldg4(rv + 16 * q);
+        if (KIND == BLOOM) {
+            // 32-bit words at or beyond l/32 are row padding: masked, so the
+            // count never exceeds l whatever the padding holds.
+            const uint32_t w0 = 4u * (uint32_t)q, wl = p.l / 32u;
+            c += __popc(a.x & b.x) + __popc(a.y & b.y) +
+                 (w0 + 2 < wl ? __popc(a.z & b.z) + __popc(a.w & b.w) : 0u);
+        } else {
+            const uint32_t i0 = 4u * (uint32_t)q;
+            c += (i0 + 0 < p.k && a.x == b.x) + (i0 + 1 < p.k && a.y == b.y) +
+                 (i0 + 2 < p.k && a.z == b.z) + (i0 + 3 < p.k && a.w == b.w);
+        }
+    }
+    return c;
+}
+
+// 1-Hash counts for one edge, whole warp (lane r holds entry r of each row).
+__device__ __forceinline__ void onehash_counts(uint32_t su, uint32_t sv, int la, int lb, int k,
+                                               int &c_union, int &K, int &c_lit) {
+    const unsigned r = lane_id();
+    const uint32_t x = su;
+    int pos = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int probe = pos + step - 1;
+        const uint32_t pv = __shfl_sync(0xffffffffu, sv, probe);
+        if (probe < lb && pv < x) pos += step;
+    }
+    const uint32_t pv = __shfl_sync(0xffffffffu, sv, pos & 31);
+    bool found = false;
+    if (pos < lb) {
+        if (pv < x)
+            ++pos;
+        else
+            found = (pv == x);
+    }
+    found = found && ((int)r < la);
+    const unsigned fm = __ballot_sync(0xffffffffu, found);
+    c_lit = __popc(fm);
+    const int U = la + lb - c_lit;
+    K = U < k ? U : k;
+    const int rank = (int)r + pos - __popc(fm & ((1u << r) - 1u));
+    c_union = __popc(__ballot_sync(0xffffffffu, found && rank < K));
+}
+
+template <int KIND, int L, bool PAIRS>
+__global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *tab = reinterpret_cast<double *>(smem);
+    uint64_t *hist = reinterpret_cast<uint64_t *>(smem + 8 * (size_t)p.table_len);
+    const bool want_hist = p.hist != nullptr;
+    for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) tab[i] = p.table[i];
+    if (want_hist)
+        for (int i = threadIdx.x; i < p.hist_len; i += blockDim.x) hist[i] = 0ull;
+    __syncthreads();
+
+    constexpr int G = 32 / L;  // groups per warp
+    const unsigned lane = lane_id();
+    const unsigned g = lane % L;
+    const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
+    const int64_t groups = (int64_t)gridDim.x * kThreads / L;
+    const uint32_t k = p.k;
+    const int hk = (int)k + 1;
+
+    // ---- work range of this group
+    int64_t e0, e1;
+    if (PAIRS) {
+        e0 = group * p.P / groups;
+        e1 = (group + 1) * p.P / groups;
+    } else {
+        const int64_t m = p.upper_off[p.n];
+        e0 = group * m / groups;
+        e1 = (group + 1) * m / groups;
+    }
+    // for KIND == ONEHASH (L == 32) the range is warp-uniform by construction
+
+    int32_t u = 0, next_off = 0, row_end = 0;
+    if (!PAIRS && e0 < e1) {
+        int32_t lo = 0, hi = p.n - 1;  // largest u with upper_off[u] <= e0
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (p.upper_off[mid] <= e0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        u = lo;
+        next_off = p.upper_off[u + 1];
+        row_end = p.row_ptr[u + 1];
+    }
+    double acc_u = 0.0;  // sum of estimates of the current u (edge source)
+    int32_t acc_vertex = -1;
+
+    // Groups of one warp may own ranges that differ by one edge: iterate the
+    // warp-wide maximum number of batches so that every shuffle is converged.
+    const int32_t my_batches = (int32_t)((e1 - e0 + kBatch - 1) / kBatch);
+    const int32_t warp_batches = __reduce_max_sync(0xffffffffu, (unsigned)my_batches);
+    for (int32_t bi = 0; bi < warp_batches; ++bi) {
+        const int64_t eb = e0 + (int64_t)bi * kBatch;
+        int32_t us[kBatch], vs[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            const int64_t e = eb + t;
+            us[t] = -1;
+            vs[t] = -1;
+            if (e < e1) {
+                if (PAIRS) {
+                    const int2 pr = __ldg(reinterpret_cast<const int2 *>(p.pairs) + e);
+                    // an id outside [0, n) makes an invalid pair: all outputs 0
+                    const bool ok = pr.x >= 0 && pr.x < p.n && pr.y >= 0 && pr.y < p.n;
+                    us[t] = ok ? pr.x : -2;
+                    vs[t] = ok ? pr.y : -2;
+                } else {
+                    while (e >= next_off) {
+                        ++u;
+                        next_off = p.upper_off[u + 1];
+                        row_end = p.row_ptr[u + 1];
+                    }
+                    us[t] = u;
+                    vs[t] = __ldg(p.col + (row_end - (next_off - (int32_t)e)));
+                }
+            }
+        }
+        int32_t du[kBatch], dv[kBatch];
+        if (p.need_deg || KIND == ONEHASH) {
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                du[t] = dv[t] = 0;
+                if (us[t] >= 0) {
+                    du[t] = __ldg(p.row_ptr + us[t] + 1) - __ldg(p.row_ptr + us[t]);
+                    dv[t] = __ldg(p.row_ptr + vs[t] + 1) - __ldg(p.row_ptr + vs[t]);
+                }
+            }
+        }
+        int32_t cnt[kBatch], Ks[kBatch], lits[kBatch];
+        if (KIND == ONEHASH) {
+            uint32_t su[kBatch], sv[kBatch];
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                su[t] = sv[t] = kEmpty;
+                if (us[t] >= 0 && lane < k) {
+                    su[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)us[t] * p.stride) + lane);
+                    sv[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)vs[t] * p.stride) + lane);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                const int la = min((int)k, du[t]), lb = min((int)k, dv[t]);
+                onehash_counts(su[t], sv[t], la, lb, (int)k, cnt[t], Ks[t], lits[t]);
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                uint32_t c = 0;
+                if (us[t] >= 0)
+                    c = lane_count<KIND, L>(p, p.data + (int64_t)us[t] * p.stride,
+                                            p.data + (int64_t)vs[t] * p.stride, g);
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+                cnt[t] = (int32_t)c;
+                if (KIND == KHASH && us[t] >= 0 && p.need_deg && (du[t] == 0 || dv[t] == 0)) cnt[t] = 0;
+            }
+        }
+        // ---- epilogue (group leader)
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            if (PAIRS && us[t] == -2 && g == 0) {
+                const int64_t e = eb + t;
+                if (p.count) p.count[e] = 0;
+                if (p.aux) p.aux[e] = 0;
+                if (p.cn) p.cn[e] = 0.0f;
+                if (p.jac) p.jac[e] = 0.0f;
+            }
+            if (us[t] < 0 || g != 0) continue;
+            const int64_t e = eb + t;
+            const int c = cnt[t];
+            double est = 0.0;
+            int64_t deg_sum = 0;
+            if (KIND == BLOOM) {
+                if (p.need_est) est = tab[c];
+                if (want_hist) atomicAdd(reinterpret_cast<unsigned long long *>(hist + c), 1ull);
+            } else if (KIND == KHASH) {
+                deg_sum = (int64_t)du[t] + dv[t];
+                if (p.need_est) est = tab[c] * (double)deg_sum;
+                if (want_hist) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + c), 1ull);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + hk + c), (unsigned long long)deg_sum);
+                }
+            } else {
+                deg_sum = (int64_t)du[t] + dv[t];
+                const int Kk = Ks[t], lit = lits[t];
+                if (p.need_est) {
+                    est = (p.est == PG_EST_1H_LITERAL) ? tab[(int)k * hk + lit] * (double)deg_sum
+                                                       : tab[Kk * hk + c] * (double)deg_sum;
+                }
+                if (want_hist) {
+                    const int bin = Kk * hk + c;
+                    const int hk2 = hk * hk;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + bin), 1ull);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + hk2 + bin), (unsigned long long)deg_sum);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * hk2 + lit), 1ull);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * hk2 + hk + lit),
+                              (unsigned long long)deg_sum);
+                }
+                if (p.aux) p.aux[e] = Kk | (lit << 16);
+            }
+            if (p.count) p.count[e] = (KIND == ONEHASH && p.est == PG_EST_1H_LITERAL) ? lits[t] : c;
+            if (p.cn) p.cn[e] = (float)est;
+            if (p.jac) {
+                const float fu = (float)du[t], fv = (float)dv[t];
+                float I = fminf(fmaxf((float)est, 0.0f), fminf(fu, fv));
+                const float den = fu + fv - I;
+                p.jac[e] = den > 0.0f ? I / den : 0.0f;
+            }
+            if (p.S) {
+                if (PAIRS) {
+                    atomicAdd(p.S + us[t], est);
+                    atomicAdd(p.S + vs[t], est);
+                } else {
+                    if (us[t] != acc_vertex) {
+                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
+                        acc_vertex = us[t];
+                        acc_u = 0.0;
+                    }
+                    acc_u += est;
+                    atomicAdd(p.S + vs[t], est);
+                }
+            }
+        }
+    }
+    if (!PAIRS && p.S && g == 0 && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
+
+    if (want_hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < p.hist_len; i += blockDim.x) {
+            const unsigned long long h = hist[i];
+            if (h) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), h);
+        }
+    }
+}
+
+// Estimator table: Bloom f(B1) for B1 = 0..l; MinHash r(K, c) = c / (K + c).
+__global__ void k_table(double *tab, int32_t kind, int32_t est, uint32_t l, uint32_t b, uint32_t k) {
+    if (kind == BLOOM) {
+        for (uint32_t j = threadIdx.x; j <= l; j += blockDim.x) {
+            if (est == PG_EST_BF_L) {
+                tab[j] = (double)j / (double)b;
+            } else {
+                const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
+                tab[j] = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
+            }
+        }
+    } else {
+        const uint32_t hk = k + 1;
+        const uint32_t rows = (kind == KHASH) ? 1u : hk;
+        for (uint32_t i = threadIdx.x; i < rows * hk; i += blockDim.x) {
+            const uint32_t K = (kind == KHASH) ? k : i / hk;
+            const uint32_t c = i % hk;
+            tab[i] = (K + c) > 0 ? (double)c / (double)(K + c) : 0.0;
+        }
+    }
+}
+
+// Graph totals from the histograms in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_tc_finalize(const uint64_t *__restrict__ hist,
+                                                     int32_t kind, int32_t est, uint32_t l,
+                                                     uint32_t b, uint32_t k,
+                                                     pg_tc_result *out) {
+    __shared__ double s_main[256], s_alt[256];
+    __shared__ unsigned long long s_edges[256], s_sum[256];
+    double main_ = 0.0, alt = 0.0;
+    unsigned long long edges = 0, sum = 0;
+    const uint32_t hk = k + 1;
+    if (kind == BLOOM) {
+        for (uint32_t j = threadIdx.x; j <= l; j += blockDim.x) {
+            const unsigned long long h = hist[j];
+            const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
+            const double f_and = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
+            const double f_l = (double)j / (double)b;
+            main_ += (double)h * (est == PG_EST_BF_L ? f_l : f_and);
+            alt += (double)h * (est == PG_EST_BF_L ? f_and : f_l);
+            edges += h;
+            sum += h * j;
+        }
+    } else if (kind == KHASH) {
+        for (uint32_t c = threadIdx.x; c < hk; c += blockDim.x) {
+            const unsigned long long h = hist[c], hd = hist[hk + c];
+            main_ += (double)hd * ((double)c / (double)(k + c));
+            edges += h;
+            sum += h * c;
+        }
+    } else {
+        const uint32_t hk2 = hk * hk;
+        for (uint32_t i = threadIdx.x; i < hk2; i += blockDim.x) {
+            const uint32_t K = i / hk, c = i % hk;
+            const unsigned long long h = hist[i], hd = hist[hk2 + i];
+            const double r = (K + c) > 0 ? (double)c / (double)(K + c) : 0.0;
+            const double lit = (i < hk) ? (double)hist[2 * hk2 + hk + i] * ((double)i / (double)(k + i)) : 0.0;
+            main_ += (est == PG_EST_1H_LITERAL) ? lit : (double)hd * r;
+            alt += (est == PG_EST_1H_LITERAL) ? (double)hd * r : lit;
+            edges += h;
+            sum += h * c;
+        }
+    }
+    s_main[threadIdx.x] = main_;
+    s_alt[threadIdx.x] = alt;
+    s_edges[threadIdx.x] = edges;
+    s_sum[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            s_main[threadIdx.x] += s_main[threadIdx.x + o];
+            s_alt[threadIdx.x] += s_alt[threadIdx.x + o];
+            s_edges[threadIdx.x] += s_edges[threadIdx.x + o];
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->edges = s_edges[0];
+        out->count_sum = s_sum[0];
+        out->exact_tc = 0;
+        out->reserved = 0;
+        out->est_tc = s_main[0] / 3.0;
+        out->est_tc_alt = s_alt[0] / 3.0;
+    }
+}
+
+__global__ void k_lcc(const int32_t *__restrict__ row_ptr, int32_t n, double *S, float *lcc,
+                      double *tri) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int32_t d = row_ptr[v + 1] - row_ptr[v];
+    const double s = S[v];
+    if (lcc) lcc[v] = d >= 2 ? (float)s / ((float)d * (float)(d - 1)) : 0.0f;
+    if (tri) tri[v] = 0.5 * s;
+}
+
+template <int KIND, int L, bool PAIRS>
+cudaError_t run(const Params &p, cudaStream_t s) {
+    const size_t smem = 8 * (size_t)p.table_len + (p.hist ? 8 * (size_t)p.hist_len : 0);
+    auto kern = k_intersect<KIND, L, PAIRS>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int grid = per_sm * device_info().sm_count;
+    kern<<<grid, kThreads, smem, s>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+int pow2_at_least(int x) {
+    int y = 1;
+    while (y < x) y <<= 1;
+    return y;
+}
+
+}  // namespace
+
+int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k) {
+    if (kind == BLOOM) return (int64_t)l + 1;
+    if (kind == KHASH) return 2 * ((int64_t)k + 1);
+    if (kind == ONEHASH) return 2 * ((int64_t)k + 1) * (k + 1) + 2 * ((int64_t)k + 1);
+    return 0;
+}
+
+static int64_t table_len(int32_t kind, uint32_t l, uint32_t k) {
+    if (kind == BLOOM) return (int64_t)l + 1;
+    if (kind == KHASH) return (int64_t)k + 1;
+    return ((int64_t)k + 1) * (k + 1);
+}
+
+// The estimator table sits at the start of the intersect workspace.
+size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k) {
+    return round_up(8 * (size_t)table_len(kind, l, k), 256);
+}
+
+cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int32_t n,
+                                const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                                const pg_sketch &sk, int32_t estimator, const EdgeOutputs &out,
+                                double *table_ws, cudaStream_t s) {
+    Params p{};
+    p.row_ptr = row_ptr;
+    p.col = col;
+    p.n = n;
+    p.upper_off = upper_off;
+    p.pairs = pairs;
+    p.P = P;
+    p.data = static_cast<const uint8_t *>(sk.data);
+    p.stride = sk.stride_bytes;
+    p.l = sk.bits;
+    p.k = sk.k;
+    p.est = estimator;
+    p.S = out.S;
+    p.cn = out.cn;
+    p.jac = out.jac;
+    p.count = out.count;
+    p.aux = out.aux;
+    p.hist = out.hist;
+    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k);
+    p.table = table_ws;
+    p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
+    p.need_est = (out.S || out.cn || out.jac) ? 1 : 0;
+    p.need_deg = (sk.kind != PG_SK_BLOOM || out.jac) ? 1 : 0;
+    k_table<<<1, 256, 0, s>>>(table_ws, sk.kind, estimator, sk.bits, sk.b, sk.k);
+    note_launch();
+    const bool pr = pairs != nullptr;
+    if (pr && P == 0) return cudaGetLastError();
+    if (sk.kind == PG_SK_BLOOM) {
+        p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
+        const int L = pow2_at_least(p.nvec) > 8 ? 8 : pow2_at_least(p.nvec);
+        switch (L) {
+            case 1: return pr ? run<BLOOM, 1, true>(p, s) : run<BLOOM, 1, false>(p, s);
+            case 2: return pr ? run<BLOOM, 2, true>(p, s) : run<BLOOM, 2, false>(p, s);
+            case 4: return pr ? run<BLOOM, 4, true>(p, s) : run<BLOOM, 4, false>(p, s);
+            default: return pr ? run<BLOOM, 8, true>(p, s) : run<BLOOM, 8, false>(p, s);
+        }
+    } else if (sk.kind == PG_SK_KHASH) {
+        p.nvec = (int32_t)((sk.k + 3) / 4);
+        const int L = pow2_at_least(p.nvec) > 16 ? 16 : pow2_at_least(p.nvec);
+        switch (L) {
+            case 1: return pr ? run<KHASH, 1, true>(p, s) : run<KHASH, 1, false>(p, s);
+            case 2: return pr ? run<KHASH, 2, true>(p, s) : run<KHASH, 2, false>(p, s);
+            case 4: return pr ? run<KHASH, 4, true>(p, s) : run<KHASH, 4, false>(p, s);
+            case 8: return pr ? run<KHASH, 8, true>(p, s) : run<KHASH, 8, false>(p, s);
+            default: return pr ? run<KHASH, 16, true>(p, s) : run<KHASH, 16, false>(p, s);
+        }
+    } else {
+        p.nvec = 0;
+        return pr ? run<ONEHASH, 32, true>(p, s) : run<ONEHASH, 32, false>(p, s);
+    }
+}
+
+cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,
+                               pg_tc_result *out, cudaStream_t s) {
+    k_tc_finalize<<<1, 256, 0, s>>>(hist, sk.kind, estimator, sk.bits, sk.b, sk.k, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lcc_finalize(const int32_t *row_ptr, int32_t n, double *S, float *lcc,
+                                double *tri, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_lcc<<<(unsigned)(((int64_t)n + 255) / 256), 256, 0, s>>>(row_ptr, n, S, lcc, tri);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace pg

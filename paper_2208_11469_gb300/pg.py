@@ -1,0 +1,383 @@
+"""Python binding of libpg (include/pg.h): argument marshalling only.
+
+Every function here passes torch device tensors to one C-ABI entry point of
+the same name (without the `pg_` prefix) on the current torch CUDA stream.
+All compute runs in the library's CUDA kernels. If the library has not been
+built, or no CUDA device is present, the calls raise — there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+import threading
+from dataclasses import dataclass, field
+
+import torch
+
+from . import build as _build
+
+# ----------------------------------------------------------------- constants
+OK = 0
+ERR = {0: "PG_OK", -1: "PG_ERR_INVALID_ARG", -2: "PG_ERR_INVALID_GRAPH", -3: "PG_ERR_TOO_LARGE",
+       -4: "PG_ERR_NO_MEMORY", -5: "PG_ERR_CUDA", -6: "PG_ERR_TIMEOUT", -7: "PG_ERR_NOT_FOUND",
+       -8: "PG_ERR_BUSY", -9: "PG_ERR_UNSUPPORTED"}
+SK_BLOOM, SK_KHASH, SK_1HASH = 1, 2, 3
+EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
+CSR_CODES = {0: "ok", 1: "bad_row_ptr", 2: "out_of_range", 3: "unsorted", 4: "self_loop", 5: "asymmetric"}
+
+# Every symbol include/pg.h declares.
+SYMBOLS = [
+    "pg_status_string", "pg_last_error", "pg_version", "pg_validate_csr", "pg_edge_index_bytes",
+    "pg_build_edge_index", "pg_edge_index_upper_off", "pg_sketch_stride",
+    "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
+    "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
+    "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze",
+]
+
+
+class PGError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {ERR.get(status, status)}: {detail}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("n", ctypes.c_int32),
+                ("nnz", ctypes.c_int64)]
+
+
+class SketchDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("bits", ctypes.c_uint32), ("b", ctypes.c_uint32),
+                ("k", ctypes.c_uint32), ("seed", ctypes.c_uint32), ("n", ctypes.c_int32),
+                ("stride_bytes", ctypes.c_int64), ("data", ctypes.c_void_p)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("tc", ctypes.c_void_p), ("lcc", ctypes.c_void_p), ("tri", ctypes.c_void_p),
+                ("edge_cn", ctypes.c_void_p), ("edge_jac", ctypes.c_void_p), ("edge_count", ctypes.c_void_p),
+                ("edge_aux", ctypes.c_void_p), ("hist", ctypes.c_void_p)]
+
+
+TC_RESULT_BYTES = 48
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpg.so (built in-tree by paper_2208_11469_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: run paper_2208_11469_gb300.build.build() first")
+            L = ctypes.CDLL(path)
+            vp, i32, i64, u32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+            P = ctypes.POINTER
+            sig = {
+                "pg_status_string": (ctypes.c_char_p, [i32]),
+                "pg_last_error": (ctypes.c_char_p, []),
+                "pg_version": (i32, []),
+                "pg_validate_csr": (i32, [P(Csr), i32, vp, vp]),
+                "pg_edge_index_bytes": (sz, [i32]),
+                "pg_build_edge_index": (i32, [P(Csr), vp, sz, vp]),
+                "pg_edge_index_upper_off": (vp, [vp]),
+                "pg_sketch_stride": (i64, [i32, u32, u32]),
+                "pg_bloom_bits_for_budget": (u32, [ctypes.c_double, i32, i64]),
+                "pg_build_workspace_bytes": (sz, [P(Csr)]),
+                "pg_build_bloom": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
+                "pg_build_minhash": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
+                "pg_hist_bins": (i64, [P(SketchDesc), i32]),
+                "pg_workspace_bytes": (sz, [P(Csr), P(SketchDesc), i32]),
+                "pg_triangle_count": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, vp, vp]),
+                "pg_clustering": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, vp, vp, vp, vp]),
+                "pg_jaccard_pairs": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, vp, vp, vp]),
+                "pg_edge_counts": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, vp, vp, vp, vp]),
+                "pg_kernel_launches": (ctypes.c_uint64, []),
+                "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise PGError(status, where, lib().pg_last_error().decode(errors="replace"))
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_bytes(nbytes: int, device) -> torch.Tensor:
+    # 16-byte aligned by the caching allocator (its blocks are 512-byte aligned)
+    return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device)
+
+
+# -------------------------------------------------------------------- graph
+@dataclass
+class Graph:
+    """An int32 CSR graph resident on the device, with its upper-edge index."""
+    row_ptr: torch.Tensor
+    col: torch.Tensor
+    index: torch.Tensor | None = None
+    _m: int | None = field(default=None, repr=False)
+
+    @property
+    def n(self) -> int:
+        return self.row_ptr.numel() - 1
+
+    @property
+    def nnz(self) -> int:
+        return self.col.numel()
+
+    @property
+    def device(self):
+        return self.row_ptr.device
+
+    def csr(self) -> Csr:
+        return Csr(self.row_ptr.data_ptr(), self.col.data_ptr() if self.col.numel() else None,
+                   self.n, self.nnz)
+
+    @property
+    def upper_off(self) -> torch.Tensor:
+        return self.index[: 4 * (self.n + 1)].view(torch.int32)
+
+    @property
+    def m(self) -> int:
+        if self._m is None:
+            self._m = int(self.upper_off[self.n].item())
+        return self._m
+
+    def degrees(self) -> torch.Tensor:
+        return (self.row_ptr[1:] - self.row_ptr[:-1])
+
+
+def graph(row_ptr: torch.Tensor, col: torch.Tensor, build_index: bool = True) -> Graph:
+    if row_ptr.dtype != torch.int32 or col.dtype != torch.int32:
+        raise TypeError("row_ptr and col must be int32")
+    if not row_ptr.is_cuda or not col.is_cuda:
+        raise ValueError("row_ptr and col must be CUDA tensors")
+    g = Graph(row_ptr.contiguous(), col.contiguous())
+    if build_index:
+        build_edge_index(g)
+    return g
+
+
+def build_edge_index(g: Graph) -> torch.Tensor:
+    L = lib()
+    nbytes = L.pg_edge_index_bytes(g.n)
+    idx = _dev_bytes(nbytes, g.device)
+    c = g.csr()
+    _check(L.pg_build_edge_index(ctypes.byref(c), _ptr(idx), idx.numel(), _stream()), "pg_build_edge_index")
+    g.index = idx
+    g._m = None
+    return idx
+
+
+def build_edge_index_into(g: Graph) -> None:
+    """Rebuild the upper-edge index in the graph's existing index buffer."""
+    c = g.csr()
+    _check(lib().pg_build_edge_index(ctypes.byref(c), _ptr(g.index), g.index.numel(), _stream()),
+           "pg_build_edge_index")
+
+
+def validate_csr(g: Graph, check_symmetry: bool = True):
+    """Returns (code_name, index) after synchronising the stream."""
+    res = torch.zeros(2, dtype=torch.int64, device=g.device)
+    c = g.csr()
+    _check(lib().pg_validate_csr(ctypes.byref(c), int(check_symmetry), _ptr(res), _stream()), "pg_validate_csr")
+    r = res.cpu()
+    return CSR_CODES.get(int(r[0]), int(r[0])), int(r[1])
+
+
+# ----------------------------------------------------------------- sketches
+@dataclass
+class Sketch:
+    kind: int
+    bits: int
+    b: int
+    k: int
+    seed: int
+    n: int
+    stride: int
+    data: torch.Tensor
+
+    def desc(self) -> SketchDesc:
+        return SketchDesc(self.kind, self.bits, self.b, self.k, self.seed & 0xFFFFFFFF, self.n,
+                          self.stride, self.data.data_ptr() if self.data.numel() else None)
+
+    def rows_u8(self) -> torch.Tensor:
+        return self.data.view(self.n, self.stride)
+
+
+def sketch_stride(kind: int, bits: int = 0, k: int = 0) -> int:
+    return int(lib().pg_sketch_stride(kind, bits, k))
+
+
+def bloom_bits_for_budget(s: float, n: int, nnz: int) -> int:
+    return int(lib().pg_bloom_bits_for_budget(float(s), n, nnz))
+
+
+def alloc_sketch(g: Graph, kind: int, *, bits: int = 0, b: int = 0, k: int = 0, seed: int = 1,
+                 stride: int | None = None) -> Sketch:
+    st = sketch_stride(kind, bits, k) if stride is None else int(stride)
+    data = _dev_bytes(g.n * st, g.device)
+    return Sketch(kind, bits, b, k, seed, g.n, st, data)
+
+
+def build_workspace_bytes(g: Graph) -> int:
+    c = g.csr()
+    return int(lib().pg_build_workspace_bytes(ctypes.byref(c)))
+
+
+def build_bloom(g: Graph, bits: int, b: int, seed: int, stride: int | None = None,
+                out: Sketch | None = None, workspace: torch.Tensor | None = None) -> Sketch:
+    sk = out if out is not None else alloc_sketch(g, SK_BLOOM, bits=bits, b=b, seed=seed, stride=stride)
+    ws = workspace if workspace is not None else _dev_bytes(build_workspace_bytes(g), g.device)
+    c, d = g.csr(), sk.desc()
+    _check(lib().pg_build_bloom(ctypes.byref(c), ctypes.byref(d), _ptr(ws), ws.numel(), _stream()), "pg_build_bloom")
+    return sk
+
+
+def build_minhash(g: Graph, kind: int, k: int, seed: int, stride: int | None = None,
+                  out: Sketch | None = None, workspace: torch.Tensor | None = None) -> Sketch:
+    sk = out if out is not None else alloc_sketch(g, kind, k=k, seed=seed, stride=stride)
+    ws = workspace if workspace is not None else _dev_bytes(build_workspace_bytes(g), g.device)
+    c, d = g.csr(), sk.desc()
+    _check(lib().pg_build_minhash(ctypes.byref(c), ctypes.byref(d), _ptr(ws), ws.numel(), _stream()),
+           "pg_build_minhash")
+    return sk
+
+
+# ----------------------------------------------------------------- analysis
+def workspace_bytes(g: Graph, sk: Sketch | None, est: int) -> int:
+    c = g.csr()
+    d = sk.desc() if sk is not None else None
+    return int(lib().pg_workspace_bytes(ctypes.byref(c), ctypes.byref(d) if d is not None else None, est))
+
+
+def hist_bins(sk: Sketch | None, est: int) -> int:
+    if sk is None:
+        return 0
+    d = sk.desc()
+    return int(lib().pg_hist_bins(ctypes.byref(d), est))
+
+
+def workspace(g: Graph, sk: Sketch | None, est: int) -> torch.Tensor:
+    return _dev_bytes(workspace_bytes(g, sk, est), g.device)
+
+
+def tc_result_buffer(device) -> torch.Tensor:
+    return torch.zeros(TC_RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_tc_result(buf: torch.Tensor) -> dict:
+    raw = bytes(buf.cpu().numpy().tobytes())
+    edges, count_sum, exact_tc, _, est_tc, est_tc_alt = struct.unpack("<QQQQdd", raw)
+    return {"edges": edges, "count_sum": count_sum, "exact_tc": exact_tc, "est_tc": est_tc,
+            "est_tc_alt": est_tc_alt}
+
+
+def _sk_args(sk):
+    if sk is None:
+        return None, None
+    d = sk.desc()
+    return d, ctypes.byref(d)
+
+
+def triangle_count(g: Graph, sk: Sketch | None, est: int, *, ws: torch.Tensor | None = None,
+                   out: torch.Tensor | None = None, read: bool = True):
+    ws = ws if ws is not None else workspace(g, sk, est)
+    out = out if out is not None else tc_result_buffer(g.device)
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_triangle_count(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(ws), ws.numel(),
+                                   _ptr(out), _stream()), "pg_triangle_count")
+    return read_tc_result(out) if read else out
+
+
+def clustering(g: Graph, sk: Sketch | None, est: int, *, want_tri: bool = True, want_tc: bool = True,
+               ws: torch.Tensor | None = None, lcc: torch.Tensor | None = None,
+               tri: torch.Tensor | None = None, tc: torch.Tensor | None = None):
+    """Returns (lcc float32[n], tri float64[n] or None, tc result buffer or None)."""
+    ws = ws if ws is not None else workspace(g, sk, est)
+    lcc = lcc if lcc is not None else torch.empty(g.n, dtype=torch.float32, device=g.device)
+    if want_tri and tri is None:
+        tri = torch.empty(g.n, dtype=torch.float64, device=g.device)
+    if want_tc and tc is None:
+        tc = tc_result_buffer(g.device)
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_clustering(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(ws), ws.numel(), _ptr(lcc),
+                               _ptr(tri) if want_tri else None, _ptr(tc) if want_tc else None, _stream()),
+           "pg_clustering")
+    return lcc, (tri if want_tri else None), (tc if want_tc else None)
+
+
+def _pairs_arg(pairs):
+    if pairs is None:
+        return None, 0
+    if pairs.dtype != torch.int32 or not pairs.is_cuda:
+        raise TypeError("pairs must be a CUDA int32 tensor of shape [P, 2]")
+    pairs = pairs.contiguous()
+    return pairs, pairs.numel() // 2
+
+
+def jaccard_pairs(g: Graph, sk: Sketch | None, est: int, pairs: torch.Tensor | None = None, *,
+                  ws: torch.Tensor | None = None, want_cn: bool = True, want_jac: bool = True):
+    pairs, P = _pairs_arg(pairs)
+    count = P if pairs is not None else g.m
+    ws = ws if ws is not None else workspace(g, sk, est)
+    cn = torch.empty(count, dtype=torch.float32, device=g.device) if want_cn else None
+    jac = torch.empty(count, dtype=torch.float32, device=g.device) if want_jac else None
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_jaccard_pairs(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(pairs), P, _ptr(ws),
+                                  ws.numel(), _ptr(cn), _ptr(jac), _stream()), "pg_jaccard_pairs")
+    return cn, jac
+
+
+def edge_counts(g: Graph, sk: Sketch | None, est: int, pairs: torch.Tensor | None = None, *,
+                want_aux: bool = False, want_hist: bool = False, ws: torch.Tensor | None = None):
+    pairs, P = _pairs_arg(pairs)
+    count = P if pairs is not None else g.m
+    ws = ws if ws is not None else workspace(g, sk, est)
+    cnt = torch.empty(count, dtype=torch.int32, device=g.device)
+    aux = torch.empty(count, dtype=torch.int32, device=g.device) if want_aux else None
+    hist = torch.empty(max(hist_bins(sk, est), 1), dtype=torch.int64, device=g.device) if want_hist else None
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_edge_counts(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(pairs), P, _ptr(ws),
+                                ws.numel(), _ptr(cnt), _ptr(aux), _ptr(hist), _stream()), "pg_edge_counts")
+    return cnt, aux, hist
+
+
+def kernel_launches() -> int:
+    return int(lib().pg_kernel_launches())
+
+
+def analyze(g: Graph, sk: Sketch | None, est: int, *, tc=None, lcc=None, tri=None, edge_cn=None,
+            edge_jac=None, edge_count=None, edge_aux=None, hist=None, ws: torch.Tensor | None = None):
+    """One fused pass (pg_analyze). Pass preallocated device tensors for the
+    outputs wanted; None leaves an output out."""
+    ws = ws if ws is not None else workspace(g, sk, est)
+    o = Outputs(*[t.data_ptr() if t is not None else None
+                  for t in (tc, lcc, tri, edge_cn, edge_jac, edge_count, edge_aux, hist)])
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_analyze(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(ws), ws.numel(), ctypes.byref(o),
+                            _stream()), "pg_analyze")

@@ -1,0 +1,110 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/pg.h declares, and rejects
+bad arguments with status codes before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2208_11469_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pg.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    import shutil
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    B.build()
+    from paper_2208_11469_gb300 import pg
+    return pg.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(pg_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_binding_symbols():
+    from paper_2208_11469_gb300 import pg
+    assert set(declared_functions()) == set(pg.SYMBOLS)
+
+
+def test_every_declared_symbol_is_exported(L):
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_version(L):
+    assert L.pg_status_string(0) == b"PG_OK"
+    assert L.pg_status_string(-4) == b"PG_ERR_NO_MEMORY"
+    assert L.pg_version() >> 16 == 1
+
+
+def test_sizing_helpers(L):
+    from paper_2208_11469_gb300 import pg
+    assert pg.sketch_stride(pg.SK_BLOOM, 448, 0) == 64
+    assert pg.sketch_stride(pg.SK_BLOOM, 192, 0) == 32
+    assert pg.sketch_stride(pg.SK_BLOOM, 960, 0) == 128
+    assert pg.sketch_stride(pg.SK_KHASH, 0, 64) == 256
+    assert pg.sketch_stride(pg.SK_1HASH, 0, 30) == 128
+    # storage budget s of the CSR bytes (Sec. V-A): R-MAT scale 24 / ef 32 at 25% and 50%
+    n, nnz = 1 << 24, 1_023_887_446
+    assert pg.bloom_bits_for_budget(0.25, n, nnz) == 448
+    assert pg.bloom_bits_for_budget(0.50, n, nnz) == 960
+    assert pg.bloom_bits_for_budget(0.25, 4096, 65536) == 128  # 136 bits -> one 64-bit word less
+    assert L.pg_edge_index_bytes(0) > 0
+
+
+def _csr(n=4, nnz=6, rp=0x1000, col=0x2000):
+    from paper_2208_11469_gb300 import pg
+    return pg.Csr(rp, col, n, nnz)
+
+
+def test_argument_errors_return_codes(L):
+    from paper_2208_11469_gb300 import pg
+    byref = ctypes.byref
+    # NULL graph
+    assert L.pg_build_edge_index(None, ctypes.c_void_p(0x1000), 1 << 20, None) == -1
+    # nnz beyond int32 CSR
+    g = _csr(nnz=1 << 31)
+    assert L.pg_build_edge_index(byref(g), ctypes.c_void_p(0x1000), 1 << 20, None) == -3
+    assert b"int32" in L.pg_last_error()
+    # index buffer too small
+    g = _csr()
+    assert L.pg_build_edge_index(byref(g), ctypes.c_void_p(0x1000), 4, None) == -4
+    # misaligned sketch data / bad parameters
+    sk = pg.SketchDesc(pg.SK_BLOOM, 100, 2, 0, 1, 4, 16, 0x3000)
+    assert L.pg_build_bloom(byref(g), byref(sk), ctypes.c_void_p(0x4000), 1 << 20, None) == -1
+    sk = pg.SketchDesc(pg.SK_BLOOM, 2048, 2, 0, 1, 4, 256, 0x3000)
+    assert L.pg_build_bloom(byref(g), byref(sk), ctypes.c_void_p(0x4000), 1 << 20, None) == -9
+    sk = pg.SketchDesc(pg.SK_BLOOM, 256, 2, 0, 1, 4, 32, 0x3008)
+    assert L.pg_build_bloom(byref(g), byref(sk), ctypes.c_void_p(0x4000), 1 << 20, None) == -1
+    sk = pg.SketchDesc(pg.SK_BLOOM, 256, 2, 0, 1, 5, 32, 0x3000)  # rows != n
+    assert L.pg_build_bloom(byref(g), byref(sk), ctypes.c_void_p(0x4000), 1 << 20, None) == -1
+    sk = pg.SketchDesc(pg.SK_1HASH, 0, 0, 64, 1, 4, 256, 0x3000)  # 1-Hash k > 32
+    assert L.pg_build_minhash(byref(g), byref(sk), ctypes.c_void_p(0x4000), 1 << 20, None) == -9
+    # estimator / sketch mismatch
+    sk = pg.SketchDesc(pg.SK_KHASH, 0, 0, 16, 1, 4, 64, 0x3000)
+    out = ctypes.c_void_p(0x5000)
+    assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk), pg.EST_BF_AND,
+                               ctypes.c_void_p(0x7000), 1 << 20, out, None) == -1
+    # workspace too small
+    need = L.pg_workspace_bytes(byref(g), byref(sk), pg.EST_KH)
+    assert need > 0
+    assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk), pg.EST_KH,
+                               ctypes.c_void_p(0x7000), need - 1, out, None) == -4
+    # missing edge index
+    assert L.pg_triangle_count(byref(g), None, byref(sk), pg.EST_KH,
+                               ctypes.c_void_p(0x7000), need, out, None) == -1
+    # unknown estimator
+    assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk), 42,
+                               ctypes.c_void_p(0x7000), need, out, None) == -1
+    # odd pairs pointer
+    assert L.pg_jaccard_pairs(byref(g), None, byref(sk), pg.EST_KH, ctypes.c_void_p(0x8004), 3,
+                              ctypes.c_void_p(0x7000), need, None, None, None) == -1
