@@ -260,6 +260,25 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
                      void *workspace, size_t workspace_bytes, const pg_outputs *out,
                      pg_stream_t stream);
 
+/* pg_triangle_count without a workspace, for callers that cannot allocate
+ * device memory (for example a plugin inside a host application whose own
+ * allocator has reserved the device memory, or a process that forbids device
+ * allocation after start-up). The paper has no counterpart: this is a
+ * packaging variant of pg_triangle_count, with the same arguments minus the
+ * workspace and the same result.
+ * Its scratch (estimator table and count histogram) lives in a 64 KiB static
+ * array of device memory inside the library, held on every GPU that loads the
+ * library until the process exits; every supported sketch fits. The exact
+ * estimator is rejected (PG_ERR_UNSUPPORTED); a sketch whose scratch would
+ * not fit returns PG_ERR_TOO_LARGE. The call allocates nothing.
+ * The first call on a device looks up the array's address with that device
+ * current; make it before any stream capture. All calls on a device share
+ * the array (cleared per call where it must start at zero): calls that
+ * overlap on the GPU race and give wrong results, so order them on one
+ * stream or synchronise between them. */
+pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *index, const pg_sketch *sk,
+                                    int32_t estimator, pg_tc_result *out, pg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

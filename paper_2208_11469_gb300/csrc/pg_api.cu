@@ -46,8 +46,6 @@ const DeviceInfo &device_info() {
     return cache[dev];
 }
 
-namespace {
-
 pg_status check_graph(const pg_csr *g) {
     PG_REQUIRE(g != nullptr, PG_ERR_INVALID_ARG, "graph is NULL");
     PG_REQUIRE(g->n >= 0, PG_ERR_INVALID_ARG, "n = %d is negative", g->n);
@@ -113,6 +111,8 @@ pg_status check_estimator(const pg_sketch *sk, int32_t est) {
         default: return set_error(PG_ERR_INVALID_ARG, "unknown estimator %d", est);
     }
 }
+
+namespace {
 
 // Workspace layout of the analysis calls:
 //   [estimator table][histogram][S: n doubles][exact path scratch]

@@ -22,6 +22,11 @@ pg_status cuda_status(cudaError_t e, const char *what);
         if (!(cond)) return ::pg::set_error(st, __VA_ARGS__);                     \
     } while (0)
 
+// Argument checks shared by the entry points (pg_api.cu).
+pg_status check_graph(const pg_csr *g);
+pg_status check_sketch(const pg_csr *g, const pg_sketch *sk);
+pg_status check_estimator(const pg_sketch *sk, int32_t est);
+
 struct DeviceInfo {
     int sm_count;
     int max_threads_per_sm;

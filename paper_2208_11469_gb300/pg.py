@@ -32,7 +32,7 @@ SYMBOLS = [
     "pg_build_edge_index", "pg_edge_index_upper_off", "pg_sketch_stride",
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
-    "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze",
+    "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
 ]
 
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
                 "pg_edge_counts": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, vp, vp, vp, vp]),
                 "pg_kernel_launches": (ctypes.c_uint64, []),
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
+                "pg_triangle_count_noalloc": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -381,3 +382,15 @@ def analyze(g: Graph, sk: Sketch | None, est: int, *, tc=None, lcc=None, tri=Non
     d, dref = _sk_args(sk)
     _check(lib().pg_analyze(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(ws), ws.numel(), ctypes.byref(o),
                             _stream()), "pg_analyze")
+
+
+def triangle_count_noalloc(g: Graph, sk: Sketch, est: int, *, out: torch.Tensor | None = None,
+                           read: bool = True):
+    """pg_triangle_count_noalloc: the sketched triangle count with its scratch
+    in the library's static device array (no workspace; see include/pg.h)."""
+    out = out if out is not None else tc_result_buffer(g.device)
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_triangle_count_noalloc(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(out), _stream()),
+           "pg_triangle_count_noalloc")
+    return read_tc_result(out) if read else out
