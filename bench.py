@@ -42,6 +42,8 @@ WORKLOADS = {
     # R-MAT scale 24, edge factor 32, Bloom at 25% of CSR bytes (b = 2), k-Hash k = 64, exact comparison
     "rmat24": dict(gen=("rmat", 24, 32, 24), budget=0.25, b=2, khash=64, onehash=None, jaccard=False),
     "rmat24_b50": dict(gen=("rmat", 24, 32, 24), budget=0.50, b=2, khash=64, onehash=None, jaccard=False),
+    # the same recipe at scale 22 (a quarter of the size): the profiling case for ncu
+    "rmat22": dict(gen=("rmat", 22, 32, 22), budget=0.25, b=2, khash=64, onehash=None, jaccard=False),
     # R-MAT scale 20, edge factor 16, Bloom at 25% (b = 2), 1-Hash k = 32, TC + LCC + per-edge Jaccard
     "rmat20": dict(gen=("rmat", 20, 16, 20), budget=0.25, b=2, khash=None, onehash=32, jaccard=True),
     # Erdos-Renyi n = 4096, average degree 16, Bloom 256 bits b = 2, k-Hash k = 16
@@ -465,10 +467,15 @@ def main():
     traffic = profiled_traffic(f"{dom}_pass_{args.workload}.md")
 
     # end to end from host buffers
-    host_rp = rp.cpu().pin_memory()
-    host_col = cl.cpu().pin_memory()
-    e2e_ms, e2e_wall, h2d, d2h = e2e_steps(pipe, host_rp, host_col, args.e2e_steps)
-    e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+    e2e = None
+    if args.e2e_steps > 0:
+        host_rp = rp.cpu().pin_memory()
+        host_col = cl.cpu().pin_memory()
+        e2e_ms, e2e_wall, h2d, d2h = e2e_steps(pipe, host_rp, host_col, args.e2e_steps)
+        e2e_ms = max_over_ranks(e2e_ms, ws, dev)
+        e2e = {"value": pipe.sketched_per_step() * ws / (e2e_ms * 1e-3), "unit": "intersections/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "wall_ms_per_step": e2e_wall}
 
     exact = None
     if not args.no_exact:
@@ -500,9 +507,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": f"k_intersect ({dom} pass, pg_analyze)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes": alg, "peak_source": peak_kind},
-            "e2e": {"value": pipe.sketched_per_step() * ws / (e2e_ms * 1e-3), "unit": "intersections/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "wall_ms_per_step": e2e_wall},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "results": res,

@@ -62,23 +62,25 @@ __device__ __forceinline__ uint4 ldg4(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
 }
 
-// Per-lane partial count of one edge for Bloom / k-Hash.
-template <int KIND, int L>
-__device__ __forceinline__ uint32_t lane_count(const Params &p, const uint8_t *ru, const uint8_t *rv,
-                                               unsigned g) {
+// Per-lane partial count of one edge for Bloom / k-Hash from the lane's
+// VPL vectors of each row (vector index g + q*L), already in registers.
+template <int KIND, int L, int VPL>
+__device__ __forceinline__ uint32_t lane_count(const Params &p, const uint4 (&a)[VPL],
+                                               const uint4 (&b)[VPL], unsigned g) {
     uint32_t c = 0;
-    for (int q = (int)g; q < p.nvec; q += L) {
-        const uint4 a = ldg4(ru + 16 * q), b = ldg4(rv + 16 * q);
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+        const uint32_t idx = g + (uint32_t)q * L;
         if (KIND == BLOOM) {
             // 32-bit words at or beyond l/32 are row padding: masked, so the
             // count never exceeds l whatever the padding holds.
-            const uint32_t w0 = 4u * (uint32_t)q, wl = p.l / 32u;
-            c += __popc(a.x & b.x) + __popc(a.y & b.y) +
-                 (w0 + 2 < wl ? __popc(a.z & b.z) + __popc(a.w & b.w) : 0u);
+            const uint32_t w0 = 4u * idx, wl = p.l / 32u;
+            c += __popc(a[q].x & b[q].x) + __popc(a[q].y & b[q].y) +
+                 (w0 + 2 < wl ? __popc(a[q].z & b[q].z) + __popc(a[q].w & b[q].w) : 0u);
         } else {
-            const uint32_t i0 = 4u * (uint32_t)q;
-            c += (i0 + 0 < p.k && a.x == b.x) + (i0 + 1 < p.k && a.y == b.y) +
-                 (i0 + 2 < p.k && a.z == b.z) + (i0 + 3 < p.k && a.w == b.w);
+            const uint32_t i0 = 4u * idx;
+            c += (i0 + 0 < p.k && a[q].x == b[q].x) + (i0 + 1 < p.k && a[q].y == b[q].y) +
+                 (i0 + 2 < p.k && a[q].z == b[q].z) + (i0 + 3 < p.k && a[q].w == b[q].w);
         }
     }
     return c;
@@ -113,7 +115,7 @@ __device__ __forceinline__ void onehash_counts(uint32_t su, uint32_t sv, int la,
     c_union = __popc(__ballot_sync(0xffffffffu, found && rank < K));
 }
 
-template <int KIND, int L, bool PAIRS>
+template <int KIND, int L, int VPL, bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
     double *tab = reinterpret_cast<double *>(smem);
@@ -219,12 +221,26 @@ __global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
                 onehash_counts(su[t], sv[t], la, lb, (int)k, cnt[t], Ks[t], lits[t]);
             }
         } else {
+            // Issue every row load of the batch before any use, so that a
+            // group keeps 2 * kBatch independent 16-byte loads in flight.
+            uint4 ra[kBatch][VPL], rb[kBatch][VPL];
 #pragma unroll
             for (int t = 0; t < kBatch; ++t) {
-                uint32_t c = 0;
-                if (us[t] >= 0)
-                    c = lane_count<KIND, L>(p, p.data + (int64_t)us[t] * p.stride,
-                                            p.data + (int64_t)vs[t] * p.stride, g);
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int idx = (int)g + q * L;
+                    if (us[t] >= 0 && idx < p.nvec) {
+                        ra[t][q] = ldg4(p.data + (int64_t)us[t] * p.stride + 16 * idx);
+                        rb[t][q] = ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx);
+                    } else {
+                        ra[t][q] = make_uint4(0u, 0u, 0u, 0u);
+                        rb[t][q] = make_uint4(1u, 1u, 1u, 1u);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kBatch; ++t) {
+                uint32_t c = lane_count<KIND, L, VPL>(p, ra[t], rb[t], g);
 #pragma unroll
                 for (int o = L / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
                 cnt[t] = (int32_t)c;
@@ -406,10 +422,10 @@ __global__ void k_lcc(const int32_t *__restrict__ row_ptr, int32_t n, double *S,
     if (tri) tri[v] = 0.5 * s;
 }
 
-template <int KIND, int L, bool PAIRS>
+template <int KIND, int L, int VPL, bool PAIRS>
 cudaError_t run(const Params &p, cudaStream_t s) {
     const size_t smem = 8 * (size_t)p.table_len + (p.hist ? 8 * (size_t)p.hist_len : 0);
-    auto kern = k_intersect<KIND, L, PAIRS>;
+    auto kern = k_intersect<KIND, L, VPL, PAIRS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -482,27 +498,33 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     const bool pr = pairs != nullptr;
     if (pr && P == 0) return cudaGetLastError();
     if (sk.kind == PG_SK_BLOOM) {
+        // l <= 1024: at most 8 vectors, one per lane
         p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
-        const int L = pow2_at_least(p.nvec) > 8 ? 8 : pow2_at_least(p.nvec);
+        const int L = pow2_at_least(p.nvec);
         switch (L) {
-            case 1: return pr ? run<BLOOM, 1, true>(p, s) : run<BLOOM, 1, false>(p, s);
-            case 2: return pr ? run<BLOOM, 2, true>(p, s) : run<BLOOM, 2, false>(p, s);
-            case 4: return pr ? run<BLOOM, 4, true>(p, s) : run<BLOOM, 4, false>(p, s);
-            default: return pr ? run<BLOOM, 8, true>(p, s) : run<BLOOM, 8, false>(p, s);
+            case 1: return pr ? run<BLOOM, 1, 1, true>(p, s) : run<BLOOM, 1, 1, false>(p, s);
+            case 2: return pr ? run<BLOOM, 2, 1, true>(p, s) : run<BLOOM, 2, 1, false>(p, s);
+            case 4: return pr ? run<BLOOM, 4, 1, true>(p, s) : run<BLOOM, 4, 1, false>(p, s);
+            default: return pr ? run<BLOOM, 8, 1, true>(p, s) : run<BLOOM, 8, 1, false>(p, s);
         }
     } else if (sk.kind == PG_SK_KHASH) {
+        // k <= 256: up to 64 vectors; 16 lanes with up to 4 vectors each
         p.nvec = (int32_t)((sk.k + 3) / 4);
         const int L = pow2_at_least(p.nvec) > 16 ? 16 : pow2_at_least(p.nvec);
-        switch (L) {
-            case 1: return pr ? run<KHASH, 1, true>(p, s) : run<KHASH, 1, false>(p, s);
-            case 2: return pr ? run<KHASH, 2, true>(p, s) : run<KHASH, 2, false>(p, s);
-            case 4: return pr ? run<KHASH, 4, true>(p, s) : run<KHASH, 4, false>(p, s);
-            case 8: return pr ? run<KHASH, 8, true>(p, s) : run<KHASH, 8, false>(p, s);
-            default: return pr ? run<KHASH, 16, true>(p, s) : run<KHASH, 16, false>(p, s);
+        if (L < 16) {
+            switch (L) {
+                case 1: return pr ? run<KHASH, 1, 1, true>(p, s) : run<KHASH, 1, 1, false>(p, s);
+                case 2: return pr ? run<KHASH, 2, 1, true>(p, s) : run<KHASH, 2, 1, false>(p, s);
+                case 4: return pr ? run<KHASH, 4, 1, true>(p, s) : run<KHASH, 4, 1, false>(p, s);
+                default: return pr ? run<KHASH, 8, 1, true>(p, s) : run<KHASH, 8, 1, false>(p, s);
+            }
         }
+        if (p.nvec <= 16) return pr ? run<KHASH, 16, 1, true>(p, s) : run<KHASH, 16, 1, false>(p, s);
+        if (p.nvec <= 32) return pr ? run<KHASH, 16, 2, true>(p, s) : run<KHASH, 16, 2, false>(p, s);
+        return pr ? run<KHASH, 16, 4, true>(p, s) : run<KHASH, 16, 4, false>(p, s);
     } else {
         p.nvec = 0;
-        return pr ? run<ONEHASH, 32, true>(p, s) : run<ONEHASH, 32, false>(p, s);
+        return pr ? run<ONEHASH, 32, 1, true>(p, s) : run<ONEHASH, 32, 1, false>(p, s);
     }
 }
 
