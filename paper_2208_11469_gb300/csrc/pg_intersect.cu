@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
         for (int i = threadIdx.x; i < p.hist_len; i += blockDim.x) hist[i] = 0ull;
     __syncthreads();
 
-    constexpr int G = 32 / L;  // groups per warp
     const unsigned lane = lane_id();
     const unsigned g = lane % L;
     const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
@@ -325,6 +324,248 @@ __global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bloom / k-Hash pass. A group of L lanes holds one sketch row as L 16-byte
+// vectors (VPL per lane); it handles B edges per iteration and each edge is
+// owned by one lane (every S = L / B lanes), which walks the index for it,
+// receives its reduced count and runs its epilogue, so the per-edge scalar
+// work is spread over the lanes instead of serialised on a group leader.
+//   iteration i:  broadcast (u_t, v_t) of the B edges  ->  issue 2B row loads
+//                 -> walk + CSR loads of iteration i+1 (overlaps the loads)
+//                 -> popcount / equality per lane -> reduce-scatter -> epilogue
+// Shared-memory histograms use 32-bit atomics; the k-Hash degree sums are kept
+// as 32-bit low words with a carry counter.
+
+// Reduce-scatter of B per-lane partials over the L lanes of a group: lane g
+// ends with the total of edge g / (L / B).
+template <int L, int B>
+__device__ __forceinline__ uint32_t reduce_scatter(uint32_t (&v)[B], unsigned g) {
+    int V = B;
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) {
+        if (V > 1) {
+            const bool hi = (g & (unsigned)o) != 0;
+#pragma unroll
+            for (int i = 0; i < B / 2; ++i) {
+                if (i < V / 2) {
+                    const uint32_t send = hi ? v[i] : v[i + V / 2];
+                    const uint32_t keep = hi ? v[i + V / 2] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            V >>= 1;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    return v[0];
+}
+
+template <int KIND, int L, int VPL, int B, bool PAIRS>
+__global__ void __launch_bounds__(kThreads) k_pass(Params p) {
+    constexpr int S = L / B;  // lanes per owned edge
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *tab = reinterpret_cast<double *>(smem);
+    uint32_t *h32 = reinterpret_cast<uint32_t *>(smem + 8 * (size_t)p.table_len);
+    const int hk = (int)p.k + 1;
+    // Bloom: counts [l+1]; k-Hash: counts [k+1], degree-sum low words [k+1], carries [k+1]
+    const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * hk;
+    const bool want_hist = p.hist != nullptr;
+    for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) tab[i] = p.table[i];
+    if (want_hist)
+        for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __syncthreads();
+
+    const unsigned lane = lane_id();
+    const unsigned g = lane % L;
+    const unsigned base = lane - g;
+    const int t_own = (int)(g / S);
+    const bool owner = (g % S) == 0;
+    const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
+    const int64_t groups = (int64_t)gridDim.x * kThreads / L;
+
+    int64_t e0, e1;
+    if (PAIRS) {
+        e0 = group * p.P / groups;
+        e1 = (group + 1) * p.P / groups;
+    } else {
+        const int64_t m = p.upper_off[p.n];
+        e0 = group * m / groups;
+        e1 = (group + 1) * m / groups;
+    }
+    // group walk state: vertex u whose upper range holds the next edge
+    int32_t gu = 0, g_next = 0, g_end = 0;
+    if (!PAIRS && e0 < e1) {
+        int32_t lo = 0, hi = p.n - 1;  // largest u with upper_off[u] <= e0
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (p.upper_off[mid] <= e0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        gu = lo;
+        g_next = p.upper_off[gu + 1];
+        g_end = p.row_ptr[gu + 1];
+    }
+
+    // Edge eb + t_own of this lane: (u, v), validity and, for owners, degrees.
+    // Returns the walk state after that edge (used by the lane owning t = B-1).
+    auto fetch = [&](int64_t eb, int32_t &u_l, int32_t &v_l, int32_t &du_l, int32_t &dv_l,
+                     int32_t &nu, int32_t &nn, int32_t &ne) {
+        const int64_t e = eb + t_own;
+        u_l = -1;
+        v_l = -1;
+        du_l = dv_l = 0;
+        nu = gu;
+        nn = g_next;
+        ne = g_end;
+        if (e < e1) {
+            if (PAIRS) {
+                const int2 pr = __ldg(reinterpret_cast<const int2 *>(p.pairs) + e);
+                const bool ok = pr.x >= 0 && pr.x < p.n && pr.y >= 0 && pr.y < p.n;
+                u_l = ok ? pr.x : -2;
+                v_l = ok ? pr.y : -2;
+                if (ok && p.need_deg && owner) {
+                    du_l = __ldg(p.row_ptr + u_l + 1) - __ldg(p.row_ptr + u_l);
+                    dv_l = __ldg(p.row_ptr + v_l + 1) - __ldg(p.row_ptr + v_l);
+                }
+            } else {
+                while (e >= nn) {
+                    ++nu;
+                    nn = p.upper_off[nu + 1];
+                    ne = p.row_ptr[nu + 1];
+                }
+                u_l = nu;
+                v_l = __ldg(p.col + (ne - (nn - (int32_t)e)));
+                if (p.need_deg && owner) {
+                    du_l = ne - __ldg(p.row_ptr + nu);
+                    dv_l = __ldg(p.row_ptr + v_l + 1) - __ldg(p.row_ptr + v_l);
+                }
+            }
+        }
+    };
+
+    double acc_u = 0.0;
+    int32_t acc_vertex = -1;
+    const int32_t my_iters = (int32_t)((e1 - e0 + B - 1) / B);
+    const int32_t warp_iters = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)(my_iters > 0 ? my_iters : 0));
+
+    int32_t cu, cv, cdu, cdv;
+    {
+        int32_t nu, nn, ne;
+        fetch(e0, cu, cv, cdu, cdv, nu, nn, ne);
+        const unsigned last = base + (unsigned)((B - 1) * S);
+        gu = __shfl_sync(0xffffffffu, nu, last);
+        g_next = __shfl_sync(0xffffffffu, nn, last);
+        g_end = __shfl_sync(0xffffffffu, ne, last);
+    }
+    for (int32_t it = 0; it < warp_iters; ++it) {
+        const int64_t eb = e0 + (int64_t)it * B;
+        // broadcast the B edges of this iteration to every lane of the group
+        int32_t us[B], vs[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+            us[t] = __shfl_sync(0xffffffffu, cu, base + (unsigned)(t * S));
+            vs[t] = __shfl_sync(0xffffffffu, cv, base + (unsigned)(t * S));
+        }
+        uint4 ra[B][VPL], rb[B][VPL];
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                const int idx = (int)g + q * L;
+                if (us[t] >= 0 && idx < p.nvec) {
+                    ra[t][q] = ldg4(p.data + (int64_t)us[t] * p.stride + 16 * idx);
+                    rb[t][q] = ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx);
+                } else {
+                    ra[t][q] = make_uint4(0u, 0u, 0u, 0u);
+                    rb[t][q] = make_uint4(1u, 1u, 1u, 1u);
+                }
+            }
+        }
+        // next iteration's edges (independent of the row loads above)
+        int32_t nu_, nv_, ndu, ndv;
+        {
+            int32_t su, sn, se;
+            fetch(eb + B, nu_, nv_, ndu, ndv, su, sn, se);
+            const unsigned last = base + (unsigned)((B - 1) * S);
+            gu = __shfl_sync(0xffffffffu, su, last);
+            g_next = __shfl_sync(0xffffffffu, sn, last);
+            g_end = __shfl_sync(0xffffffffu, se, last);
+        }
+        uint32_t part[B];
+#pragma unroll
+        for (int t = 0; t < B; ++t) part[t] = lane_count<KIND, L, VPL>(p, ra[t], rb[t], g);
+        uint32_t c = reduce_scatter<L, B>(part, g);
+
+        // ---- epilogue: the owner lane of each edge
+        const int64_t e = eb + t_own;
+        if (owner && cu == -2) {  // invalid pair
+            if (p.count) p.count[e] = 0;
+            if (p.cn) p.cn[e] = 0.0f;
+            if (p.jac) p.jac[e] = 0.0f;
+        }
+        if (owner && cu >= 0) {
+            if (KIND == KHASH && p.need_deg && (cdu == 0 || cdv == 0)) c = 0;
+            double est = 0.0;
+            if (KIND == BLOOM) {
+                if (p.need_est) est = tab[c];
+                if (want_hist) atomicAdd(h32 + c, 1u);
+            } else {
+                const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
+                if (p.need_est) est = tab[c] * (double)ds;
+                if (want_hist) {
+                    atomicAdd(h32 + c, 1u);
+                    const uint32_t old = atomicAdd(h32 + hk + c, ds);
+                    if (old + ds < old) atomicAdd(h32 + 2 * hk + c, 1u);
+                }
+            }
+            if (p.count) p.count[e] = (int32_t)c;
+            if (p.cn) p.cn[e] = (float)est;
+            if (p.jac) {
+                const float fu = (float)cdu, fv = (float)cdv;
+                const float I = fminf(fmaxf((float)est, 0.0f), fminf(fu, fv));
+                const float den = fu + fv - I;
+                p.jac[e] = den > 0.0f ? I / den : 0.0f;
+            }
+            if (p.S) {
+                if (PAIRS) {
+                    atomicAdd(p.S + cu, est);
+                    atomicAdd(p.S + cv, est);
+                } else {
+                    if (cu != acc_vertex) {
+                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
+                        acc_vertex = cu;
+                        acc_u = 0.0;
+                    }
+                    acc_u += est;
+                    atomicAdd(p.S + cv, est);
+                }
+            }
+        }
+        cu = nu_;
+        cv = nv_;
+        cdu = ndu;
+        cdv = ndv;
+    }
+    if (!PAIRS && p.S && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
+
+    if (want_hist) {
+        __syncthreads();
+        if (KIND == BLOOM) {
+            for (int i = threadIdx.x; i < h32_len; i += blockDim.x)
+                if (h32[i]) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), (unsigned long long)h32[i]);
+        } else {
+            for (int i = threadIdx.x; i < hk; i += blockDim.x) {
+                if (h32[i]) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), (unsigned long long)h32[i]);
+                const unsigned long long d = (unsigned long long)h32[hk + i] | ((unsigned long long)h32[2 * hk + i] << 32);
+                if (d) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + hk + i), d);
+            }
+        }
+    }
+}
+
 // Estimator table: Bloom f(B1) for B1 = 0..l; MinHash r(K, c) = c / (K + c).
 __global__ void k_table(double *tab, int32_t kind, int32_t est, uint32_t l, uint32_t b, uint32_t k) {
     if (kind == BLOOM) {
@@ -440,6 +681,24 @@ cudaError_t run(const Params &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int KIND, int L, int VPL, int B, bool PAIRS>
+cudaError_t run_pass(const Params &p, cudaStream_t s) {
+    const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
+    const size_t smem = 8 * (size_t)p.table_len + (p.hist ? 4 * (size_t)h32_len : 0);
+    auto kern = k_pass<KIND, L, VPL, B, PAIRS>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<per_sm * device_info().sm_count, kThreads, smem, s>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
 int pow2_at_least(int x) {
     int y = 1;
     while (y < x) y <<= 1;
@@ -498,30 +757,30 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     const bool pr = pairs != nullptr;
     if (pr && P == 0) return cudaGetLastError();
     if (sk.kind == PG_SK_BLOOM) {
-        // l <= 1024: at most 8 vectors, one per lane
+        // l <= 1024: at most 8 vectors, one per lane; B = min(L, 4) edges per group
         p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
         const int L = pow2_at_least(p.nvec);
         switch (L) {
-            case 1: return pr ? run<BLOOM, 1, 1, true>(p, s) : run<BLOOM, 1, 1, false>(p, s);
-            case 2: return pr ? run<BLOOM, 2, 1, true>(p, s) : run<BLOOM, 2, 1, false>(p, s);
-            case 4: return pr ? run<BLOOM, 4, 1, true>(p, s) : run<BLOOM, 4, 1, false>(p, s);
-            default: return pr ? run<BLOOM, 8, 1, true>(p, s) : run<BLOOM, 8, 1, false>(p, s);
+            case 1: return pr ? run_pass<BLOOM, 1, 1, 1, true>(p, s) : run_pass<BLOOM, 1, 1, 1, false>(p, s);
+            case 2: return pr ? run_pass<BLOOM, 2, 1, 2, true>(p, s) : run_pass<BLOOM, 2, 1, 2, false>(p, s);
+            case 4: return pr ? run_pass<BLOOM, 4, 1, 4, true>(p, s) : run_pass<BLOOM, 4, 1, 4, false>(p, s);
+            default: return pr ? run_pass<BLOOM, 8, 1, 4, true>(p, s) : run_pass<BLOOM, 8, 1, 4, false>(p, s);
         }
     } else if (sk.kind == PG_SK_KHASH) {
-        // k <= 256: up to 64 vectors; 16 lanes with up to 4 vectors each
+        // k <= 256: up to 64 vectors; at most 16 lanes with up to 4 vectors each
         p.nvec = (int32_t)((sk.k + 3) / 4);
         const int L = pow2_at_least(p.nvec) > 16 ? 16 : pow2_at_least(p.nvec);
         if (L < 16) {
             switch (L) {
-                case 1: return pr ? run<KHASH, 1, 1, true>(p, s) : run<KHASH, 1, 1, false>(p, s);
-                case 2: return pr ? run<KHASH, 2, 1, true>(p, s) : run<KHASH, 2, 1, false>(p, s);
-                case 4: return pr ? run<KHASH, 4, 1, true>(p, s) : run<KHASH, 4, 1, false>(p, s);
-                default: return pr ? run<KHASH, 8, 1, true>(p, s) : run<KHASH, 8, 1, false>(p, s);
+                case 1: return pr ? run_pass<KHASH, 1, 1, 1, true>(p, s) : run_pass<KHASH, 1, 1, 1, false>(p, s);
+                case 2: return pr ? run_pass<KHASH, 2, 1, 2, true>(p, s) : run_pass<KHASH, 2, 1, 2, false>(p, s);
+                case 4: return pr ? run_pass<KHASH, 4, 1, 4, true>(p, s) : run_pass<KHASH, 4, 1, 4, false>(p, s);
+                default: return pr ? run_pass<KHASH, 8, 1, 4, true>(p, s) : run_pass<KHASH, 8, 1, 4, false>(p, s);
             }
         }
-        if (p.nvec <= 16) return pr ? run<KHASH, 16, 1, true>(p, s) : run<KHASH, 16, 1, false>(p, s);
-        if (p.nvec <= 32) return pr ? run<KHASH, 16, 2, true>(p, s) : run<KHASH, 16, 2, false>(p, s);
-        return pr ? run<KHASH, 16, 4, true>(p, s) : run<KHASH, 16, 4, false>(p, s);
+        if (p.nvec <= 16) return pr ? run_pass<KHASH, 16, 1, 4, true>(p, s) : run_pass<KHASH, 16, 1, 4, false>(p, s);
+        if (p.nvec <= 32) return pr ? run_pass<KHASH, 16, 2, 2, true>(p, s) : run_pass<KHASH, 16, 2, 2, false>(p, s);
+        return pr ? run_pass<KHASH, 16, 4, 1, true>(p, s) : run_pass<KHASH, 16, 4, 1, false>(p, s);
     } else {
         p.nvec = 0;
         return pr ? run<ONEHASH, 32, 1, true>(p, s) : run<ONEHASH, 32, 1, false>(p, s);
