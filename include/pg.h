@@ -104,12 +104,15 @@ pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *resu
 
 /* ------------------------------------------------------------ edge index */
 /* The upper-edge index: upper_off[u] = number of upper edges (u', v) with
- * u' < u, upper_off[n] = m (undirected edges). It enumerates each edge once
- * for the sum over E of the TC estimator (Sec. VII) and fixes the per-edge
- * output order. Built once per graph and reused by every analysis call. */
-size_t pg_edge_index_bytes(int32_t n);
-/* index: DEVICE buffer of pg_edge_index_bytes(g->n) bytes, 16-byte aligned.
- * Overwritten. Valid for this graph until the graph changes. */
+ * u' < u, upper_off[n] = m (undirected edges), and the upper-edge list itself
+ * (u, v, d_u and d_v of every edge, in order). It enumerates each edge once for the
+ * sum over E of the TC estimator (Sec. VII) and fixes the per-edge output
+ * order. Built once per graph and reused by every analysis call. Its size
+ * bounds m by nnz / 2 (a symmetric CSR); for a CSR that is not symmetric the
+ * list is cut there (pg_validate_csr reports such graphs). */
+size_t pg_edge_index_bytes(int32_t n, int64_t nnz);
+/* index: DEVICE buffer of pg_edge_index_bytes(g->n, g->nnz) bytes, 16-byte
+ * aligned. Overwritten. Valid for this graph until the graph changes. */
 pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes,
                               pg_stream_t stream);
 /* The DEVICE address of upper_off (int32 [n+1]) inside an index buffer. */

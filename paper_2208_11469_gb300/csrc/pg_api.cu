@@ -205,7 +205,9 @@ pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *resu
     return PG_OK;
 }
 
-size_t pg_edge_index_bytes(int32_t n) { return n < 0 ? 0 : upper_index_bytes(n); }
+size_t pg_edge_index_bytes(int32_t n, int64_t nnz) {
+    return (n < 0 || nnz < 0) ? 0 : upper_index_bytes(n, nnz);
+}
 
 const int32_t *pg_edge_index_upper_off(const void *index) {
     return static_cast<const int32_t *>(index);
@@ -216,12 +218,9 @@ pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes, 
     if (st) return st;
     PG_REQUIRE(index != nullptr && aligned16(index), PG_ERR_INVALID_ARG,
                "index must be a 16-byte aligned device buffer");
-    PG_REQUIRE(index_bytes >= upper_index_bytes(g->n), PG_ERR_NO_MEMORY,
-               "index has %zu bytes, needs %zu", index_bytes, upper_index_bytes(g->n));
-    int32_t *upper_off = static_cast<int32_t *>(index);
-    int32_t *scratch = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(index) +
-                                                   round_up(4 * ((size_t)g->n + 1), 256));
-    PG_TRY_CUDA(launch_upper_index(g->row_ptr, g->col, g->n, upper_off, scratch, stream),
+    PG_REQUIRE(index_bytes >= upper_index_bytes(g->n, g->nnz), PG_ERR_NO_MEMORY,
+               "index has %zu bytes, needs %zu", index_bytes, upper_index_bytes(g->n, g->nnz));
+    PG_TRY_CUDA(launch_upper_index(g->row_ptr, g->col, g->n, g->nnz, index, stream),
                 "pg_build_edge_index");
     return PG_OK;
 }
@@ -310,7 +309,8 @@ pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch 
     if (st) return st;
     PG_REQUIRE(out != nullptr && (reinterpret_cast<uintptr_t>(out) & 7u) == 0, PG_ERR_INVALID_ARG,
                "out must be an 8-byte aligned device pg_tc_result");
-    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
+    const int32_t *upper_off = ix.upper_off;
     if (estimator == PG_EST_EXACT) {
         PG_TRY_CUDA(launch_exact_tc(g->row_ptr, g->col, g->n, g->nnz, upper_off, w.exact, nullptr,
                                     out, stream),
@@ -321,7 +321,7 @@ pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch 
     launch_fill_u64(w.hist, bins, 0, stream);
     EdgeOutputs eo{};
     eo.hist = w.hist;
-    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk,
                                     estimator, eo, w.table, stream),
                 "pg_triangle_count");
     PG_TRY_CUDA(launch_tc_finalize(w.hist, *sk, estimator, out, stream), "pg_triangle_count");
@@ -340,7 +340,8 @@ pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk,
                    (reinterpret_cast<uintptr_t>(tc) & 7u) == 0 &&
                    (reinterpret_cast<uintptr_t>(lcc) & 3u) == 0,
                PG_ERR_INVALID_ARG, "misaligned output pointer");
-    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
+    const int32_t *upper_off = ix.upper_off;
     double *S = tri ? tri : w.S;
     launch_fill_f64(S, (size_t)g->n, 0.0, stream);
     if (estimator == PG_EST_EXACT) {
@@ -354,7 +355,7 @@ pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk,
             eo.hist = w.hist;
             launch_fill_u64(w.hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
         }
-        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk,
                                         estimator, eo, w.table, stream),
                     "pg_clustering");
         if (tc) PG_TRY_CUDA(launch_tc_finalize(w.hist, *sk, estimator, tc, stream), "pg_clustering");
@@ -385,12 +386,12 @@ pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *
     EdgeOutputs eo{};
     eo.cn = cn;
     eo.jac = jac;
-    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
     if (estimator == PG_EST_EXACT) {
-        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, pairs, P, eo, stream),
+        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, pairs, P, eo, stream),
                     "pg_jaccard_pairs(exact)");
     } else {
-        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, pairs, P, *sk,
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, pairs, P, *sk,
                                         estimator, eo, w.table, stream),
                     "pg_jaccard_pairs");
     }
@@ -406,9 +407,9 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
     if (st) return st;
     EdgeOutputs eo{};
     eo.count = count;
-    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
     if (estimator == PG_EST_EXACT) {
-        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, pairs, P, eo, stream),
+        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, pairs, P, eo, stream),
                     "pg_edge_counts(exact)");
         return PG_OK;
     }
@@ -419,7 +420,7 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
         eo.hist = hist;
         launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
     }
-    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, pairs, P, *sk, estimator,
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, pairs, P, *sk, estimator,
                                     eo, w.table, stream),
                 "pg_edge_counts");
     return PG_OK;
@@ -440,7 +441,8 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
                    (reinterpret_cast<uintptr_t>(out->edge_count) & 3u) == 0 &&
                    (reinterpret_cast<uintptr_t>(out->edge_aux) & 3u) == 0,
                PG_ERR_INVALID_ARG, "misaligned output pointer");
-    const int32_t *upper_off = static_cast<const int32_t *>(index);
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
+    const int32_t *upper_off = ix.upper_off;
     const bool want_vertex = out->lcc || out->tri;
     double *S = want_vertex ? (out->tri ? out->tri : w.S) : nullptr;
     if (S) launch_fill_f64(S, (size_t)g->n, 0.0, stream);
@@ -454,7 +456,7 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
             eo.cn = out->edge_cn;
             eo.jac = out->edge_jac;
             eo.count = out->edge_count;
-            PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, eo,
+            PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, nullptr, 0, eo,
                                            stream),
                         "pg_analyze(exact)");
         }
@@ -470,7 +472,7 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
             eo.hist = hist;
             launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
         }
-        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, upper_off, nullptr, 0, *sk,
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk,
                                         estimator, eo, w.table, stream),
                     "pg_analyze");
         if (out->tc) PG_TRY_CUDA(launch_tc_finalize(hist, *sk, estimator, out->tc, stream), "pg_analyze");

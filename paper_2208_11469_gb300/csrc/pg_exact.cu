@@ -181,12 +181,11 @@ __global__ void k_exact_result(const unsigned long long *tc_total, const int32_t
     out->est_tc_alt = 0.0;
 }
 
-// Exact |N_u ∩ N_v| per upper edge or pair over the full rows.
+// Exact |N_u ∩ N_v| per upper edge (lists eu/ev) or pair over the full rows.
 template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restrict__ row_ptr,
                                                           const int32_t *__restrict__ col,
-                                                          int32_t n,
-                                                          const int32_t *__restrict__ upper_off,
+                                                          int32_t n, EdgeIndex ix,
                                                           const int32_t *__restrict__ pairs,
                                                           int64_t P, int32_t *count, float *cn,
                                                           float *jac) {
@@ -194,28 +193,15 @@ __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restr
     const unsigned g = lane % kL;
     const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / kL;
     const int64_t groups = (int64_t)gridDim.x * kThreads / kL;
-    const int64_t total = PAIRS ? P : (int64_t)upper_off[n];
+    int64_t total = PAIRS ? P : (int64_t)ix.upper_off[n];
+    if (!PAIRS && total > ix.cap) total = ix.cap;
     const int64_t e0 = group * total / groups, e1 = (group + 1) * total / groups;
-    int32_t u = 0, next = 0, row_end = 0;
-    if (!PAIRS && e0 < e1) {
-        int32_t lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (upper_off[mid] <= e0)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        u = lo;
-        next = upper_off[u + 1];
-        row_end = row_ptr[u + 1];
-    }
     const int32_t my_n = (int32_t)(e1 - e0);
     const int32_t warp_n = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)(my_n > 0 ? my_n : 0));
     for (int32_t i = 0; i < warp_n; ++i) {
         const int64_t e = e0 + i;
         uint32_t c = 0;
-        int32_t a = 0, b = 0, du = 0, dv = 0;
+        int32_t du = 0, dv = 0;
         if (e < e1) {
             int32_t x, y;
             bool ok = true;
@@ -226,18 +212,13 @@ __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restr
                 x = pr.x;
                 y = pr.y;
             } else {
-                while (e >= next) {
-                    ++u;
-                    next = upper_off[u + 1];
-                    row_end = row_ptr[u + 1];
-                }
-                x = u;
-                y = __ldg(col + (row_end - (next - (int32_t)e)));
+                x = __ldg(ix.eu + e);
+                y = __ldg(ix.ev + e);
             }
             if (ok) {
-                a = __ldg(row_ptr + x);
+                const int32_t a = __ldg(row_ptr + x);
                 du = __ldg(row_ptr + x + 1) - a;
-                b = __ldg(row_ptr + y);
+                const int32_t b = __ldg(row_ptr + y);
                 dv = __ldg(row_ptr + y + 1) - b;
                 c = lane_intersect(col + a, du, col + b, dv, g, [](int32_t) {});
             }
@@ -296,20 +277,18 @@ cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t 
 }
 
 cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                               const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                               const EdgeIndex &ix, const int32_t *pairs, int64_t P,
                                const EdgeOutputs &out, cudaStream_t s) {
     if (pairs) {
         if (P > 0)
         {
-            k_exact_pairs<true><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, upper_off,
-                                                                       pairs, P, out.count, out.cn,
-                                                                       out.jac);
+            k_exact_pairs<true><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, ix, pairs, P,
+                                                                       out.count, out.cn, out.jac);
             note_launch();
         }
     } else if (n > 0) {
-        k_exact_pairs<false><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, upper_off,
-                                                                    nullptr, 0, out.count, out.cn,
-                                                                    out.jac);
+        k_exact_pairs<false><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, ix, nullptr, 0,
+                                                                    out.count, out.cn, out.jac);
         note_launch();
     }
     return cudaGetLastError();

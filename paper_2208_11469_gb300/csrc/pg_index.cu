@@ -52,6 +52,89 @@ __global__ void k_upper_degree(const int32_t *__restrict__ row_ptr,
     out[u] = end - lo;
 }
 
+// The upper-edge list: for upper edge e = (u, v) the index stores eu[e] = u,
+// ev[e] = v and the degrees edu[e] = d_u, edv[e] = d_v, so passes read them as
+// coalesced streams instead of gathering row offsets. The output is cut into
+// chunks of kListChunk edges; a warp takes a chunk, finds the row holding its
+// first edge (a 32-way search over upper_off), and then walks windows of 32
+// consecutive rows: each lane locates the window row of its output position
+// with a binary search over the 32 row ends held in the lanes. Stores are
+// coalesced and each lane has kListUnroll independent loads in flight. Writes
+// at or beyond cap are dropped.
+constexpr int32_t kListChunk = 4096;
+constexpr int kListUnroll = 4;
+
+__global__ void __launch_bounds__(256) k_upper_lists(const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col, int32_t n,
+                                                     const int32_t *__restrict__ upper_off,
+                                                     int32_t *__restrict__ eu, int32_t *__restrict__ ev,
+                                                     int32_t *__restrict__ edu, int32_t *__restrict__ edv,
+                                                     int64_t cap) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    int64_t m = upper_off[n];
+    if (m > cap) m = cap;
+    const int64_t chunks = (m + kListChunk - 1) / kListChunk;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
+        const int64_t c0 = c * kListChunk;
+        const int64_t c1 = c0 + kListChunk < m ? c0 + kListChunk : m;
+        // largest u in [0, n-1] with upper_off[u] <= c0, by a 32-way search
+        int64_t lo = 0, hi = (int64_t)n - 1;
+        while (hi - lo >= 32) {
+            const int64_t step = (hi - lo + 31) / 32;
+            const int64_t probe = lo + (int64_t)lane * step;
+            const bool ok = probe <= hi && upper_off[probe] <= c0;
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            const int last = 31 - __clz((int)bal);  // lane 0 always satisfies ok
+            const int64_t nlo = lo + (int64_t)last * step;
+            hi = (nlo + step - 1 < hi) ? nlo + step - 1 : hi;
+            lo = nlo;
+        }
+        {
+            const int64_t probe = lo + lane;
+            const bool ok = probe <= hi && upper_off[probe] <= c0;
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            lo += 31 - __clz((int)bal);
+        }
+        int64_t u0 = lo;
+        int64_t e = c0;
+        while (e < c1) {
+            // window rows u0 .. u0+31 (lanes past n repeat row n-1)
+            const int64_t ul = u0 + lane < n ? u0 + lane : (int64_t)n - 1;
+            const int32_t off_end = upper_off[ul + 1];
+            const int32_t rp_end = row_ptr[ul + 1];
+            const int32_t deg = rp_end - row_ptr[ul];
+            const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
+            const int64_t wend = c1 < (int64_t)last_end ? c1 : (int64_t)last_end;
+            for (int64_t base = e; base < wend; base += 32 * kListUnroll) {
+#pragma unroll
+                for (int j = 0; j < kListUnroll; ++j) {
+                    const int64_t ee = base + 32 * j + lane;
+                    int r = 0;  // window rows whose upper range ends at or before ee
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int32_t pr = __shfl_sync(0xffffffffu, off_end, r + step - 1);
+                        if ((int64_t)pr <= ee) r += step;
+                    }
+                    const int rr = r < 31 ? r : 31;
+                    const int32_t oe = __shfl_sync(0xffffffffu, off_end, rr);
+                    const int32_t re = __shfl_sync(0xffffffffu, rp_end, rr);
+                    const int32_t du = __shfl_sync(0xffffffffu, deg, rr);
+                    if (ee < wend) {
+                        const int32_t v = __ldg(col + (re - (oe - (int32_t)ee)));
+                        eu[ee] = (int32_t)(u0 + rr);
+                        ev[ee] = v;
+                        edu[ee] = du;
+                        edv[ee] = __ldg(row_ptr + v + 1) - __ldg(row_ptr + v);
+                    }
+                }
+            }
+            e = wend > e ? wend : e;
+            u0 += 32;
+        }
+    }
+}
+
 // Block-wide exclusive scan of kScanItems values per thread.
 __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v[kScanItems], int32_t *smem_warp,
                                                         int32_t &block_total) {
@@ -237,10 +320,33 @@ void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s) {
 
 static int64_t scan_tiles(int64_t count) { return (count + kScanTile - 1) / kScanTile; }
 
-size_t upper_index_bytes(int32_t n) {
+// Index layout: upper_off [n+1] | scan scratch | eu | ev | edu | edv [cap each], where
+// cap = nnz / 2 + 1 bounds m for a symmetric CSR (m = nnz / 2). For a CSR
+// that is not symmetric the lists are cut at cap (consumers read at most cap
+// edges); pg_validate_csr detects such graphs.
+static int64_t list_cap(int64_t nnz) { return nnz / 2 + 1; }
+
+size_t upper_index_bytes(int32_t n, int64_t nnz) {
     const int64_t count = (int64_t)n + 1;
     return round_up(sizeof(int32_t) * (size_t)count, 256) +
-           round_up(sizeof(int32_t) * (size_t)scan_tiles(count), 256);
+           round_up(sizeof(int32_t) * (size_t)scan_tiles(count), 256) +
+           4 * round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
+}
+
+EdgeIndex edge_index_view(const void *index, int32_t n, int64_t nnz) {
+    const int64_t count = (int64_t)n + 1;
+    const uint8_t *b = static_cast<const uint8_t *>(index);
+    EdgeIndex x;
+    x.upper_off = reinterpret_cast<const int32_t *>(b);
+    size_t off = round_up(sizeof(int32_t) * (size_t)count, 256) +
+                 round_up(sizeof(int32_t) * (size_t)scan_tiles(count), 256);
+    x.eu = reinterpret_cast<const int32_t *>(b + off);
+    const size_t lb = round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
+    x.ev = reinterpret_cast<const int32_t *>(b + off + lb);
+    x.edu = reinterpret_cast<const int32_t *>(b + off + 2 * lb);
+    x.edv = reinterpret_cast<const int32_t *>(b + off + 3 * lb);
+    x.cap = list_cap(nnz);
+    return x;
 }
 
 size_t scan_scratch_bytes(int64_t count) {
@@ -257,12 +363,26 @@ cudaError_t launch_exclusive_scan(int32_t *data, int64_t count, int32_t *scratch
     return cudaGetLastError();
 }
 
-cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                               int32_t *upper_off, int32_t *scratch, cudaStream_t s) {
+cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                               void *index, cudaStream_t s) {
     const int64_t count = (int64_t)n + 1;
+    int32_t *upper_off = static_cast<int32_t *>(index);
+    int32_t *scratch = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(index) +
+                                                   round_up(sizeof(int32_t) * (size_t)count, 256));
     k_upper_degree<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(row_ptr, col, n, upper_off);
     note_launch();
-    return launch_exclusive_scan(upper_off, count, scratch, s);
+    cudaError_t e = launch_exclusive_scan(upper_off, count, scratch, s);
+    if (e != cudaSuccess || n == 0) return e;
+    EdgeIndex x = edge_index_view(index, n, nnz);
+    const int64_t chunks = (nnz / 2 + kListChunk) / kListChunk;
+    int64_t grid = (chunks + 7) / 8;
+    if (grid > 8 * device_info().sm_count) grid = 8 * device_info().sm_count;
+    if (grid < 1) grid = 1;
+    k_upper_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, upper_off, const_cast<int32_t *>(x.eu),
+                                                 const_cast<int32_t *>(x.ev), const_cast<int32_t *>(x.edu),
+                                                 const_cast<int32_t *>(x.edv), x.cap);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,

@@ -78,12 +78,22 @@ __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 // Defined in pg_index.cu
 void launch_fill_u64(uint64_t *p, size_t count, uint64_t value, cudaStream_t s);
 void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s);
-size_t upper_index_bytes(int32_t n);
+// View of an upper-edge index buffer (pg_build_edge_index).
+struct EdgeIndex {
+    const int32_t *upper_off;  // [n+1]
+    const int32_t *eu;         // [cap] u of upper edge e
+    const int32_t *ev;         // [cap] v of upper edge e
+    const int32_t *edu;        // [cap] degree of u
+    const int32_t *edv;        // [cap] degree of v
+    int64_t cap;               // list capacity; edges read = min(upper_off[n], cap)
+};
+size_t upper_index_bytes(int32_t n, int64_t nnz);
+EdgeIndex edge_index_view(const void *index, int32_t n, int64_t nnz);
 size_t scan_scratch_bytes(int64_t count);
 // In-place exclusive prefix sum of count int32 values (scratch: scan_scratch_bytes).
 cudaError_t launch_exclusive_scan(int32_t *data, int64_t count, int32_t *scratch, cudaStream_t s);
-cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                               int32_t *upper_off, int32_t *scratch, cudaStream_t s);
+cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
+                               void *index, cudaStream_t s);
 cudaError_t launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
                             int check_symmetry, int64_t *result, cudaStream_t s);
 
@@ -113,7 +123,7 @@ size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k);
 // Enqueue the estimator-table kernel (into table_ws) and the intersection
 // kernel over every upper edge (pairs == nullptr) or over P pairs.
 cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                                const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                                const EdgeIndex &ix, const int32_t *pairs, int64_t P,
                                 const pg_sketch &sk, int32_t estimator, const EdgeOutputs &out,
                                 double *table_ws, cudaStream_t s);
 cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,
@@ -132,7 +142,7 @@ cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t 
 // Exact |N_u ∩ N_v| per upper edge (pairs == nullptr) or per pair, into
 // out.count / out.cn / out.jac.
 cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                               const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                               const EdgeIndex &ix, const int32_t *pairs, int64_t P,
                                const EdgeOutputs &out, cudaStream_t s);
 
 }  // namespace pg

@@ -1,24 +1,21 @@
 // Sketch intersection, per-edge estimation and reduction (Sec. IV, Sec. VII).
 //
-// One kernel serves all three sketch kinds and both work sources:
-//   - every upper edge (u < v) of the graph, enumerated from the upper-edge
-//     index, or
-//   - an explicit list of vertex pairs.
-// A "group" of L lanes handles one edge at a time; each lane loads 16-byte
-// vectors of the two sketch rows (the row of u repeats along a CSR row and
-// is served from L1), the group reduces its partial count with shuffles and
-// the epilogue turns the integer count into the estimate:
-//   Bloom : B1 = popcount(B_u AND B_v)          -> Eq. (bf_int) / Eq. (limit_xs)
-//   k-Hash: c = #{i : min_i(u) = min_i(v)}        -> Eq. (est_int_mh)
-//   1-Hash: c_union, K, c_lit (warp-wide merge)   -> Sec. IV-D
+// The work is a list of (u, v) pairs: every upper edge of the graph (the
+// lists eu/ev of the edge index, u < v, CSR order) or an explicit pair list.
+// Each warp takes a contiguous range of the list, so the (u, v) loads are
+// coalesced streams and consecutive edges share u.
+//   Bloom / k-Hash (k_pass): a group of L lanes holds one sketch row as 16-byte
+//     vectors; per iteration it loads the rows of B edges, counts
+//     popcount(B_u AND B_v) or equal minima lane-wise and reduce-scatters the
+//     counts so that each edge ends on its owner lane, which runs the
+//     epilogue (estimate, histogram, per-vertex sums, outputs).
+//   1-Hash (k_onehash): one warp per edge, lane r holds entry r of each row;
+//     the counts come from a warp-wide merge (reading C of the design notes).
 // Graph totals come from exact integer histograms of the counts (block-local
-// in shared memory, merged with integer atomics) and one fixed-order double
-// dot product in k_tc_finalize, so they are deterministic. Per-vertex sums
-// S_v = sum over incident edges of the estimate use double atomics.
-//
-// Edge partition: the m upper edges are split into Q equal contiguous ranges,
-// one per group (a persistent grid of Q groups); each group binary-searches
-// its first vertex once and then walks the index.
+// in shared memory with 32-bit atomics, merged with 64-bit integer atomics)
+// and one fixed-order double dot product in k_tc_finalize, so they are
+// deterministic. Per-vertex sums S_v of the estimate use double atomics: one
+// per edge at v, one per run of equal u in the warp at u.
 #include "pg_internal.cuh"
 
 namespace pg {
@@ -26,8 +23,9 @@ namespace pg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBatch = 4;      // edges a group has in flight
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+__host__ __device__ __forceinline__ int32_t round_up4(int32_t x) { return (x + 3) & ~3; }
 
 enum Kind { BLOOM = PG_SK_BLOOM, KHASH = PG_SK_KHASH, ONEHASH = PG_SK_1HASH };
 
@@ -36,7 +34,12 @@ struct Params {
     const int32_t *col;
     int32_t n;
     const int32_t *upper_off;
-    const int32_t *pairs;
+    const int32_t *eu;      // upper-edge list (edge source)
+    const int32_t *ev;
+    const int32_t *edu;     // degrees of u and v per upper edge
+    const int32_t *edv;
+    int64_t cap;            // list capacity
+    const int32_t *pairs;   // pair list (pair source)
     int64_t P;
     const uint8_t *data;
     int64_t stride;
@@ -57,6 +60,23 @@ struct Params {
     uint64_t *hist;
     int32_t hist_len;   // number of uint64 bins
 };
+
+// Per-vertex sums and per-edge estimates avoid double-precision arithmetic
+// on the hot path (double throughput is a small fraction of the integer and
+// float pipes on this GPU): an estimate is carried as the exact integer
+// V = round(value * 2^42) (kFixBits), summed with integer adds, and turned
+// into a double for the atomic by integer bit manipulation (truncating, so
+// within 2^-52 relative).
+constexpr int kFixBits = 42;
+
+__device__ __forceinline__ double fx_to_f64(unsigned long long x) {
+    if (x == 0ull) return 0.0;
+    const int e = 63 - __clzll((long long)x);  // position of the leading one
+    const unsigned long long mant = e >= 52 ? (x >> (e - 52)) : (x << (52 - e));
+    const unsigned long long bits =
+        ((unsigned long long)(e - kFixBits + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
 
 __device__ __forceinline__ uint4 ldg4(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -115,215 +135,6 @@ __device__ __forceinline__ void onehash_counts(uint32_t su, uint32_t sv, int la,
     c_union = __popc(__ballot_sync(0xffffffffu, found && rank < K));
 }
 
-template <int KIND, int L, int VPL, bool PAIRS>
-__global__ void __launch_bounds__(kThreads) k_intersect(Params p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    double *tab = reinterpret_cast<double *>(smem);
-    uint64_t *hist = reinterpret_cast<uint64_t *>(smem + 8 * (size_t)p.table_len);
-    const bool want_hist = p.hist != nullptr;
-    for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) tab[i] = p.table[i];
-    if (want_hist)
-        for (int i = threadIdx.x; i < p.hist_len; i += blockDim.x) hist[i] = 0ull;
-    __syncthreads();
-
-    const unsigned lane = lane_id();
-    const unsigned g = lane % L;
-    const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
-    const int64_t groups = (int64_t)gridDim.x * kThreads / L;
-    const uint32_t k = p.k;
-    const int hk = (int)k + 1;
-
-    // ---- work range of this group
-    int64_t e0, e1;
-    if (PAIRS) {
-        e0 = group * p.P / groups;
-        e1 = (group + 1) * p.P / groups;
-    } else {
-        const int64_t m = p.upper_off[p.n];
-        e0 = group * m / groups;
-        e1 = (group + 1) * m / groups;
-    }
-    // for KIND == ONEHASH (L == 32) the range is warp-uniform by construction
-
-    int32_t u = 0, next_off = 0, row_end = 0;
-    if (!PAIRS && e0 < e1) {
-        int32_t lo = 0, hi = p.n - 1;  // largest u with upper_off[u] <= e0
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (p.upper_off[mid] <= e0)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        u = lo;
-        next_off = p.upper_off[u + 1];
-        row_end = p.row_ptr[u + 1];
-    }
-    double acc_u = 0.0;  // sum of estimates of the current u (edge source)
-    int32_t acc_vertex = -1;
-
-    // Groups of one warp may own ranges that differ by one edge: iterate the
-    // warp-wide maximum number of batches so that every shuffle is converged.
-    const int32_t my_batches = (int32_t)((e1 - e0 + kBatch - 1) / kBatch);
-    const int32_t warp_batches = __reduce_max_sync(0xffffffffu, (unsigned)my_batches);
-    for (int32_t bi = 0; bi < warp_batches; ++bi) {
-        const int64_t eb = e0 + (int64_t)bi * kBatch;
-        int32_t us[kBatch], vs[kBatch];
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            const int64_t e = eb + t;
-            us[t] = -1;
-            vs[t] = -1;
-            if (e < e1) {
-                if (PAIRS) {
-                    const int2 pr = __ldg(reinterpret_cast<const int2 *>(p.pairs) + e);
-                    // an id outside [0, n) makes an invalid pair: all outputs 0
-                    const bool ok = pr.x >= 0 && pr.x < p.n && pr.y >= 0 && pr.y < p.n;
-                    us[t] = ok ? pr.x : -2;
-                    vs[t] = ok ? pr.y : -2;
-                } else {
-                    while (e >= next_off) {
-                        ++u;
-                        next_off = p.upper_off[u + 1];
-                        row_end = p.row_ptr[u + 1];
-                    }
-                    us[t] = u;
-                    vs[t] = __ldg(p.col + (row_end - (next_off - (int32_t)e)));
-                }
-            }
-        }
-        int32_t du[kBatch], dv[kBatch];
-        if (p.need_deg || KIND == ONEHASH) {
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                du[t] = dv[t] = 0;
-                if (us[t] >= 0) {
-                    du[t] = __ldg(p.row_ptr + us[t] + 1) - __ldg(p.row_ptr + us[t]);
-                    dv[t] = __ldg(p.row_ptr + vs[t] + 1) - __ldg(p.row_ptr + vs[t]);
-                }
-            }
-        }
-        int32_t cnt[kBatch], Ks[kBatch], lits[kBatch];
-        if (KIND == ONEHASH) {
-            uint32_t su[kBatch], sv[kBatch];
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                su[t] = sv[t] = kEmpty;
-                if (us[t] >= 0 && lane < k) {
-                    su[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)us[t] * p.stride) + lane);
-                    sv[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)vs[t] * p.stride) + lane);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                const int la = min((int)k, du[t]), lb = min((int)k, dv[t]);
-                onehash_counts(su[t], sv[t], la, lb, (int)k, cnt[t], Ks[t], lits[t]);
-            }
-        } else {
-            // Issue every row load of the batch before any use, so that a
-            // group keeps 2 * kBatch independent 16-byte loads in flight.
-            uint4 ra[kBatch][VPL], rb[kBatch][VPL];
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-#pragma unroll
-                for (int q = 0; q < VPL; ++q) {
-                    const int idx = (int)g + q * L;
-                    if (us[t] >= 0 && idx < p.nvec) {
-                        ra[t][q] = ldg4(p.data + (int64_t)us[t] * p.stride + 16 * idx);
-                        rb[t][q] = ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx);
-                    } else {
-                        ra[t][q] = make_uint4(0u, 0u, 0u, 0u);
-                        rb[t][q] = make_uint4(1u, 1u, 1u, 1u);
-                    }
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < kBatch; ++t) {
-                uint32_t c = lane_count<KIND, L, VPL>(p, ra[t], rb[t], g);
-#pragma unroll
-                for (int o = L / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-                cnt[t] = (int32_t)c;
-                if (KIND == KHASH && us[t] >= 0 && p.need_deg && (du[t] == 0 || dv[t] == 0)) cnt[t] = 0;
-            }
-        }
-        // ---- epilogue (group leader)
-#pragma unroll
-        for (int t = 0; t < kBatch; ++t) {
-            if (PAIRS && us[t] == -2 && g == 0) {
-                const int64_t e = eb + t;
-                if (p.count) p.count[e] = 0;
-                if (p.aux) p.aux[e] = 0;
-                if (p.cn) p.cn[e] = 0.0f;
-                if (p.jac) p.jac[e] = 0.0f;
-            }
-            if (us[t] < 0 || g != 0) continue;
-            const int64_t e = eb + t;
-            const int c = cnt[t];
-            double est = 0.0;
-            int64_t deg_sum = 0;
-            if (KIND == BLOOM) {
-                if (p.need_est) est = tab[c];
-                if (want_hist) atomicAdd(reinterpret_cast<unsigned long long *>(hist + c), 1ull);
-            } else if (KIND == KHASH) {
-                deg_sum = (int64_t)du[t] + dv[t];
-                if (p.need_est) est = tab[c] * (double)deg_sum;
-                if (want_hist) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + c), 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + hk + c), (unsigned long long)deg_sum);
-                }
-            } else {
-                deg_sum = (int64_t)du[t] + dv[t];
-                const int Kk = Ks[t], lit = lits[t];
-                if (p.need_est) {
-                    est = (p.est == PG_EST_1H_LITERAL) ? tab[(int)k * hk + lit] * (double)deg_sum
-                                                       : tab[Kk * hk + c] * (double)deg_sum;
-                }
-                if (want_hist) {
-                    const int bin = Kk * hk + c;
-                    const int hk2 = hk * hk;
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + bin), 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + hk2 + bin), (unsigned long long)deg_sum);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * hk2 + lit), 1ull);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(hist + 2 * hk2 + hk + lit),
-                              (unsigned long long)deg_sum);
-                }
-                if (p.aux) p.aux[e] = Kk | (lit << 16);
-            }
-            if (p.count) p.count[e] = (KIND == ONEHASH && p.est == PG_EST_1H_LITERAL) ? lits[t] : c;
-            if (p.cn) p.cn[e] = (float)est;
-            if (p.jac) {
-                const float fu = (float)du[t], fv = (float)dv[t];
-                float I = fminf(fmaxf((float)est, 0.0f), fminf(fu, fv));
-                const float den = fu + fv - I;
-                p.jac[e] = den > 0.0f ? I / den : 0.0f;
-            }
-            if (p.S) {
-                if (PAIRS) {
-                    atomicAdd(p.S + us[t], est);
-                    atomicAdd(p.S + vs[t], est);
-                } else {
-                    if (us[t] != acc_vertex) {
-                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
-                        acc_vertex = us[t];
-                        acc_u = 0.0;
-                    }
-                    acc_u += est;
-                    atomicAdd(p.S + vs[t], est);
-                }
-            }
-        }
-    }
-    if (!PAIRS && p.S && g == 0 && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
-
-    if (want_hist) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < p.hist_len; i += blockDim.x) {
-            const unsigned long long h = hist[i];
-            if (h) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), h);
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Bloom / k-Hash pass. A group of L lanes holds one sketch row as L 16-byte
 // vectors (VPL per lane); it handles B edges per iteration and each edge is
@@ -361,17 +172,94 @@ __device__ __forceinline__ uint32_t reduce_scatter(uint32_t (&v)[B], unsigned g)
     return v[0];
 }
 
-template <int KIND, int L, int VPL, int B, bool PAIRS>
-__global__ void __launch_bounds__(kThreads) k_pass(Params p) {
-    constexpr int S = L / B;  // lanes per owned edge
+// Work range of one warp: a contiguous slice of the edge or pair list.
+template <bool PAIRS>
+__device__ __forceinline__ void warp_range(const Params &p, int64_t &w0, int64_t &w1) {
+    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
+    int64_t total;
+    if (PAIRS) {
+        total = p.P;
+    } else {
+        total = p.upper_off[p.n];
+        if (total > p.cap) total = p.cap;
+    }
+    w0 = warp * total / warps;
+    w1 = (warp + 1) * total / warps;
+}
+
+// (u, v) of work item e (u = -1: beyond the range; -2: pair with an id outside
+// [0, n)) and, when want_deg, the two degrees.
+template <bool PAIRS>
+__device__ __forceinline__ void item(const Params &p, int64_t e, int64_t w1, bool want_deg, int32_t &u,
+                                     int32_t &v, int32_t &du, int32_t &dv) {
+    u = v = -1;
+    du = dv = 0;
+    if (e < w1) {
+        if (PAIRS) {
+            const int2 pr = __ldg(reinterpret_cast<const int2 *>(p.pairs) + e);
+            const bool ok = pr.x >= 0 && pr.x < p.n && pr.y >= 0 && pr.y < p.n;
+            u = ok ? pr.x : -2;
+            v = ok ? pr.y : -2;
+            if (ok && want_deg) {
+                du = __ldg(p.row_ptr + u + 1) - __ldg(p.row_ptr + u);
+                dv = __ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v);
+            }
+        } else {
+            u = __ldg(p.eu + e);
+            v = __ldg(p.ev + e);
+            if (want_deg) {
+                du = __ldg(p.edu + e);
+                dv = __ldg(p.edv + e);
+            }
+        }
+    }
+}
+
+// Per-vertex sums at u for the edge source: lanes hold consecutive edges, so
+// equal u form runs of lanes; a segmented suffix sum of the fixed-point
+// values leaves each run's total on its first lane, which issues one atomic.
+__device__ __forceinline__ void add_u_runs(double *S, int32_t key, unsigned long long val) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long ov = __shfl_down_sync(0xffffffffu, val, o);
+        const int32_t ok = __shfl_down_sync(0xffffffffu, key, o);
+        if (lane + (unsigned)o < 32u && ok == key) val += ov;
+    }
+    const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (key >= 0 && (lane == 0 || prev != key) && val != 0ull) atomicAdd(S + key, fx_to_f64(val));
+}
+
+// Layout of a Bloom / k-Hash pass: a group of L lanes holds a sketch row as
+// L x VPL 16-byte vectors and owns B items per iteration (every L/B-th lane
+// owns one: it fetches the item, receives its reduced count and runs its
+// epilogue). Rows are loaded SB items at a time (registers bound SB); with
+// UREUSE the row of u stays in registers while u repeats. MINB = blocks per SM
+// the register budget is sized for.
+template <int KIND, int L, int VPL, int B, int SB, bool UREUSE, int MINB, bool PAIRS>
+__global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
+    constexpr int S = L / B;          // lanes per owned item
+    constexpr int E = (32 / L) * B;   // items per warp iteration
     extern __shared__ __align__(16) unsigned char smem[];
+    // tables: estimate (double), estimate * 2^42 (integer), estimate (float)
     double *tab = reinterpret_cast<double *>(smem);
-    uint32_t *h32 = reinterpret_cast<uint32_t *>(smem + 8 * (size_t)p.table_len);
+    unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
+    float *tabF = reinterpret_cast<float *>(smem + 16 * (size_t)p.table_len);
+    uint32_t *h32 = reinterpret_cast<uint32_t *>(smem + 20 * (size_t)round_up4(p.table_len));
     const int hk = (int)p.k + 1;
     // Bloom: counts [l+1]; k-Hash: counts [k+1], degree-sum low words [k+1], carries [k+1]
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * hk;
     const bool want_hist = p.hist != nullptr;
-    for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) tab[i] = p.table[i];
+    {
+        const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
+        const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
+        for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) {
+            tab[i] = p.table[i];
+            tabV[i] = gV[i];
+            tabF[i] = gF[i];
+        }
+    }
     if (want_hist)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
     __syncthreads();
@@ -379,142 +267,90 @@ __global__ void __launch_bounds__(kThreads) k_pass(Params p) {
     const unsigned lane = lane_id();
     const unsigned g = lane % L;
     const unsigned base = lane - g;
-    const int t_own = (int)(g / S);
     const bool owner = (g % S) == 0;
-    const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / L;
-    const int64_t groups = (int64_t)gridDim.x * kThreads / L;
+    const int slot = (int)(lane / L) * B + (int)(g / S);  // item offset inside an iteration
 
-    int64_t e0, e1;
-    if (PAIRS) {
-        e0 = group * p.P / groups;
-        e1 = (group + 1) * p.P / groups;
-    } else {
-        const int64_t m = p.upper_off[p.n];
-        e0 = group * m / groups;
-        e1 = (group + 1) * m / groups;
-    }
-    // group walk state: vertex u whose upper range holds the next edge
-    int32_t gu = 0, g_next = 0, g_end = 0;
-    if (!PAIRS && e0 < e1) {
-        int32_t lo = 0, hi = p.n - 1;  // largest u with upper_off[u] <= e0
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (p.upper_off[mid] <= e0)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        gu = lo;
-        g_next = p.upper_off[gu + 1];
-        g_end = p.row_ptr[gu + 1];
-    }
-
-    // Edge eb + t_own of this lane: (u, v), validity and, for owners, degrees.
-    // Returns the walk state after that edge (used by the lane owning t = B-1).
-    auto fetch = [&](int64_t eb, int32_t &u_l, int32_t &v_l, int32_t &du_l, int32_t &dv_l,
-                     int32_t &nu, int32_t &nn, int32_t &ne) {
-        const int64_t e = eb + t_own;
-        u_l = -1;
-        v_l = -1;
-        du_l = dv_l = 0;
-        nu = gu;
-        nn = g_next;
-        ne = g_end;
-        if (e < e1) {
-            if (PAIRS) {
-                const int2 pr = __ldg(reinterpret_cast<const int2 *>(p.pairs) + e);
-                const bool ok = pr.x >= 0 && pr.x < p.n && pr.y >= 0 && pr.y < p.n;
-                u_l = ok ? pr.x : -2;
-                v_l = ok ? pr.y : -2;
-                if (ok && p.need_deg && owner) {
-                    du_l = __ldg(p.row_ptr + u_l + 1) - __ldg(p.row_ptr + u_l);
-                    dv_l = __ldg(p.row_ptr + v_l + 1) - __ldg(p.row_ptr + v_l);
-                }
-            } else {
-                while (e >= nn) {
-                    ++nu;
-                    nn = p.upper_off[nu + 1];
-                    ne = p.row_ptr[nu + 1];
-                }
-                u_l = nu;
-                v_l = __ldg(p.col + (ne - (nn - (int32_t)e)));
-                if (p.need_deg && owner) {
-                    du_l = ne - __ldg(p.row_ptr + nu);
-                    dv_l = __ldg(p.row_ptr + v_l + 1) - __ldg(p.row_ptr + v_l);
-                }
-            }
-        }
-    };
-
-    double acc_u = 0.0;
-    int32_t acc_vertex = -1;
-    const int32_t my_iters = (int32_t)((e1 - e0 + B - 1) / B);
-    const int32_t warp_iters = (int32_t)__reduce_max_sync(0xffffffffu, (unsigned)(my_iters > 0 ? my_iters : 0));
+    int64_t w0, w1;
+    warp_range<PAIRS>(p, w0, w1);
+    const int32_t iters = (int32_t)((w1 - w0 + E - 1) / E);
 
     int32_t cu, cv, cdu, cdv;
-    {
-        int32_t nu, nn, ne;
-        fetch(e0, cu, cv, cdu, cdv, nu, nn, ne);
-        const unsigned last = base + (unsigned)((B - 1) * S);
-        gu = __shfl_sync(0xffffffffu, nu, last);
-        g_next = __shfl_sync(0xffffffffu, nn, last);
-        g_end = __shfl_sync(0xffffffffu, ne, last);
-    }
-    for (int32_t it = 0; it < warp_iters; ++it) {
-        const int64_t eb = e0 + (int64_t)it * B;
-        // broadcast the B edges of this iteration to every lane of the group
-        int32_t us[B], vs[B];
+    item<PAIRS>(p, w0 + slot, w1, p.need_deg != 0, cu, cv, cdu, cdv);
+    int32_t cur_u = -1;  // UREUSE: vertex whose row slice is in cur_row
+    uint4 cur_row[VPL];
 #pragma unroll
-        for (int t = 0; t < B; ++t) {
-            us[t] = __shfl_sync(0xffffffffu, cu, base + (unsigned)(t * S));
-            vs[t] = __shfl_sync(0xffffffffu, cv, base + (unsigned)(t * S));
-        }
-        uint4 ra[B][VPL], rb[B][VPL];
+    for (int q = 0; q < VPL; ++q) cur_row[q] = make_uint4(0u, 0u, 0u, 0u);
+    for (int32_t it = 0; it < iters; ++it) {
+        const int64_t eb = w0 + (int64_t)it * E;
+        // next iteration's work items (independent of this iteration's row loads)
+        int32_t nu, nv, ndu, ndv;
+        item<PAIRS>(p, eb + E + slot, w1, p.need_deg != 0, nu, nv, ndu, ndv);
+        uint32_t part[B];
 #pragma unroll
-        for (int t = 0; t < B; ++t) {
+        for (int sb = 0; sb < B; sb += SB) {
+            int32_t us[SB], vs[SB];
 #pragma unroll
-            for (int q = 0; q < VPL; ++q) {
-                const int idx = (int)g + q * L;
-                if (us[t] >= 0 && idx < p.nvec) {
-                    ra[t][q] = ldg4(p.data + (int64_t)us[t] * p.stride + 16 * idx);
-                    rb[t][q] = ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx);
-                } else {
-                    ra[t][q] = make_uint4(0u, 0u, 0u, 0u);
-                    rb[t][q] = make_uint4(1u, 1u, 1u, 1u);
+            for (int t = 0; t < SB; ++t) {
+                us[t] = __shfl_sync(0xffffffffu, cu, base + (unsigned)((sb + t) * S));
+                vs[t] = __shfl_sync(0xffffffffu, cv, base + (unsigned)((sb + t) * S));
+            }
+            // issue every row load of the sub-batch before any use
+            uint4 ra[SB][VPL], rb[SB][VPL];
+#pragma unroll
+            for (int t = 0; t < SB; ++t) {
+                const bool reuse = UREUSE && us[t] == cur_u;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const int idx = (int)g + q * L;
+                    const bool in = us[t] >= 0 && idx < p.nvec;
+                    rb[t][q] = in ? ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx) : make_uint4(1u, 1u, 1u, 1u);
+                    if (reuse)
+                        ra[t][q] = cur_row[q];
+                    else
+                        ra[t][q] = in ? ldg4(p.data + (int64_t)us[t] * p.stride + 16 * idx) : make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < SB; ++t) part[sb + t] = lane_count<KIND, L, VPL>(p, ra[t], rb[t], g);
+            if (UREUSE) {
+#pragma unroll
+                for (int t = 0; t < SB; ++t) {
+                    if (us[t] >= 0) {
+                        cur_u = us[t];
+#pragma unroll
+                        for (int q = 0; q < VPL; ++q) cur_row[q] = ra[t][q];
+                    }
                 }
             }
         }
-        // next iteration's edges (independent of the row loads above)
-        int32_t nu_, nv_, ndu, ndv;
-        {
-            int32_t su, sn, se;
-            fetch(eb + B, nu_, nv_, ndu, ndv, su, sn, se);
-            const unsigned last = base + (unsigned)((B - 1) * S);
-            gu = __shfl_sync(0xffffffffu, su, last);
-            g_next = __shfl_sync(0xffffffffu, sn, last);
-            g_end = __shfl_sync(0xffffffffu, se, last);
-        }
-        uint32_t part[B];
-#pragma unroll
-        for (int t = 0; t < B; ++t) part[t] = lane_count<KIND, L, VPL>(p, ra[t], rb[t], g);
         uint32_t c = reduce_scatter<L, B>(part, g);
 
         // ---- epilogue: the owner lane of each edge
-        const int64_t e = eb + t_own;
+        const int64_t e = eb + slot;
+        unsigned long long V = 0ull;  // estimate * 2^42
         if (owner && cu == -2) {  // invalid pair
             if (p.count) p.count[e] = 0;
             if (p.cn) p.cn[e] = 0.0f;
             if (p.jac) p.jac[e] = 0.0f;
         }
         if (owner && cu >= 0) {
-            if (KIND == KHASH && p.need_deg && (cdu == 0 || cdv == 0)) c = 0;
-            double est = 0.0;
+            if (KIND == KHASH && (cdu == 0 || cdv == 0)) c = 0;
+            float est_f = 0.0f;
+            double est_d = 0.0;
             if (KIND == BLOOM) {
-                if (p.need_est) est = tab[c];
+                if (p.need_est) {
+                    V = tabV[c];
+                    est_d = tab[c];
+                    est_f = tabF[c];
+                }
                 if (want_hist) atomicAdd(h32 + c, 1u);
             } else {
                 const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
-                if (p.need_est) est = tab[c] * (double)ds;
+                if (p.need_est) {
+                    V = tabV[c] * (unsigned long long)ds;
+                    est_d = p.S ? fx_to_f64(V) : 0.0;
+                    est_f = tabF[c] * (float)ds;
+                }
                 if (want_hist) {
                     atomicAdd(h32 + c, 1u);
                     const uint32_t old = atomicAdd(h32 + hk + c, ds);
@@ -522,34 +358,25 @@ __global__ void __launch_bounds__(kThreads) k_pass(Params p) {
                 }
             }
             if (p.count) p.count[e] = (int32_t)c;
-            if (p.cn) p.cn[e] = (float)est;
+            if (p.cn) p.cn[e] = est_f;
             if (p.jac) {
                 const float fu = (float)cdu, fv = (float)cdv;
-                const float I = fminf(fmaxf((float)est, 0.0f), fminf(fu, fv));
+                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
                 const float den = fu + fv - I;
                 p.jac[e] = den > 0.0f ? I / den : 0.0f;
             }
             if (p.S) {
-                if (PAIRS) {
-                    atomicAdd(p.S + cu, est);
-                    atomicAdd(p.S + cv, est);
-                } else {
-                    if (cu != acc_vertex) {
-                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
-                        acc_vertex = cu;
-                        acc_u = 0.0;
-                    }
-                    acc_u += est;
-                    atomicAdd(p.S + cv, est);
-                }
+                atomicAdd(p.S + cv, est_d);
+                if (PAIRS) atomicAdd(p.S + cu, est_d);
             }
         }
-        cu = nu_;
-        cv = nv_;
+        // non-owner lanes carry their owner's u (cu) with a zero value, so runs stay contiguous
+        if (!PAIRS && p.S) add_u_runs(p.S, cu, owner ? V : 0ull);
+        cu = nu;
+        cv = nv;
         cdu = ndu;
         cdv = ndv;
     }
-    if (!PAIRS && p.S && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, acc_u);
 
     if (want_hist) {
         __syncthreads();
@@ -566,25 +393,335 @@ __global__ void __launch_bounds__(kThreads) k_pass(Params p) {
     }
 }
 
-// Estimator table: Bloom f(B1) for B1 = 0..l; MinHash r(K, c) = c / (K + c).
-__global__ void k_table(double *tab, int32_t kind, int32_t est, uint32_t l, uint32_t b, uint32_t k) {
-    if (kind == BLOOM) {
-        for (uint32_t j = threadIdx.x; j <= l; j += blockDim.x) {
-            if (est == PG_EST_BF_L) {
-                tab[j] = (double)j / (double)b;
-            } else {
-                const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
-                tab[j] = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
+// ---------------------------------------------------------------------------
+// Lean passes for the common row widths (edge source). Lane l of a warp owns
+// item eb + l of a 32-item iteration; a group of L lanes reads one row per
+// step as L 16-byte vectors, so an iteration is L steps of 32 / L items.
+//   Bloom (L = l / 128 vectors per row, last vector possibly half used): the
+//     group's popcount partials are summed with log2(L) xor-shuffles.
+//   k-Hash (L = 16 lanes, k / 4 of them hold a vector): each lane counts its
+//     equal minima; one warp-wide integer reduction returns the counts of
+//     both 16-lane groups at once (group 1's count in the upper 16 bits).
+// The row of u stays in registers while u repeats (u is non-decreasing along
+// the list); the epilogue is the same as in k_pass, run by every lane for its
+// own item.
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
+    // W: 32-bit words of the row payload (l / 32 for Bloom, k for k-Hash)
+    constexpr int NV = (W + 3) / 4;  // vectors per row
+    static_assert(NV <= L, "a row must fit one vector per lane");
+    constexpr bool kRedux = (KIND == KHASH && L == 16);
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *tab = reinterpret_cast<double *>(smem);
+    unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
+    float *tabF = reinterpret_cast<float *>(smem + 16 * (size_t)p.table_len);
+    uint32_t *h32 = reinterpret_cast<uint32_t *>(smem + 20 * (size_t)round_up4(p.table_len));
+    const int hk = (int)p.k + 1;
+    const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * hk;
+    const bool want_hist = p.hist != nullptr;
+    {
+        const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
+        const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
+        for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) {
+            tab[i] = p.table[i];
+            tabV[i] = gV[i];
+            tabF[i] = gF[i];
+        }
+    }
+    if (want_hist)
+        for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __syncthreads();
+
+    const unsigned lane = lane_id();
+    const unsigned g = lane & (L - 1);
+    const int grp = (int)(lane / L);
+    // Lanes past the row's vectors read vector 0 (inside the row) and count nothing.
+    const int vidx = (int)g < NV ? (int)g : 0;
+    // Word j of this lane's vector is payload iff 4g + j < W (compile-time for full rows).
+    const bool ok0 = (int)(4 * g + 0) < W, ok1 = (int)(4 * g + 1) < W;
+    const bool ok2 = (int)(4 * g + 2) < W, ok3 = (int)(4 * g + 3) < W;
+    const uint32_t grp_shift = (uint32_t)grp * 16u;
+    const bool need_deg = p.need_deg != 0;
+    const uint8_t *rowbase = p.data + 16 * vidx;
+
+    int64_t w0, w1;
+    warp_range<false>(p, w0, w1);
+    const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
+
+    int32_t cu, cv, cdu, cdv;
+    item<false>(p, w0 + lane, w1, need_deg, cu, cv, cdu, cdv);
+    int32_t cur_u = -1;
+    uint4 cur_row = make_uint4(0u, 0u, 0u, 0u);
+
+    for (int32_t it = 0; it < iters; ++it) {
+        const int64_t eb = w0 + (int64_t)it * 32;
+        int32_t nu, nv, ndu, ndv;
+        item<false>(p, eb + 32 + lane, w1, need_deg, nu, nv, ndu, ndv);
+        uint32_t c = 0;
+#pragma unroll
+        for (int s0 = 0; s0 < L; s0 += SB) {
+            int32_t us[SB];
+            uint4 ra[SB], rb[SB];
+#pragma unroll
+            for (int t = 0; t < SB; ++t) {
+                const unsigned src = (unsigned)(grp * L + s0 + t);  // lane owning this step's item
+                us[t] = __shfl_sync(0xffffffffu, cu, src);
+                const int32_t vt = max(__shfl_sync(0xffffffffu, cv, src), 0);  // past the range: row 0, unused
+                rb[t] = ldg4(rowbase + (int64_t)vt * p.stride);
+                if (UREUSE && us[t] == cur_u)
+                    ra[t] = cur_row;
+                else
+                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], 0) * p.stride);
+            }
+#pragma unroll
+            for (int t = 0; t < SB; ++t) {
+                uint32_t v;
+                if (KIND == BLOOM) {
+                    v = (ok0 ? __popc(ra[t].x & rb[t].x) : 0u) + (ok1 ? __popc(ra[t].y & rb[t].y) : 0u) +
+                        (ok2 ? __popc(ra[t].z & rb[t].z) : 0u) + (ok3 ? __popc(ra[t].w & rb[t].w) : 0u);
+                } else {
+                    v = (ok0 && ra[t].x == rb[t].x) + (ok1 && ra[t].y == rb[t].y) +
+                        (ok2 && ra[t].z == rb[t].z) + (ok3 && ra[t].w == rb[t].w);
+                }
+                if (kRedux) {
+                    // counts of both 16-lane groups in one reduction (group 1 in the upper half)
+                    const uint32_t r = __reduce_add_sync(0xffffffffu, v << grp_shift);
+                    if ((int)g == s0 + t) c = (r >> grp_shift) & 0xFFFFu;
+                } else {
+#pragma unroll
+                    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if ((int)g == s0 + t) c = v;
+                }
+            }
+            if (UREUSE && us[SB - 1] >= 0) {
+                cur_u = us[SB - 1];
+                cur_row = ra[SB - 1];
             }
         }
-    } else {
-        const uint32_t hk = k + 1;
-        const uint32_t rows = (kind == KHASH) ? 1u : hk;
-        for (uint32_t i = threadIdx.x; i < rows * hk; i += blockDim.x) {
-            const uint32_t K = (kind == KHASH) ? k : i / hk;
-            const uint32_t c = i % hk;
-            tab[i] = (K + c) > 0 ? (double)c / (double)(K + c) : 0.0;
+
+        // ---- epilogue: every lane, for its own item
+        const int64_t e = eb + lane;
+        unsigned long long V = 0ull;
+        if (cu >= 0) {
+            if (KIND == KHASH && (cdu == 0 || cdv == 0)) c = 0;
+            float est_f = 0.0f;
+            double est_d = 0.0;
+            if (KIND == BLOOM) {
+                if (p.need_est) {
+                    V = tabV[c];
+                    est_d = tab[c];
+                    est_f = tabF[c];
+                }
+                if (want_hist) atomicAdd(h32 + c, 1u);
+            } else {
+                const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
+                if (p.need_est) {
+                    V = tabV[c] * (unsigned long long)ds;
+                    est_d = p.S ? fx_to_f64(V) : 0.0;
+                    est_f = tabF[c] * (float)ds;
+                }
+                if (want_hist) {
+                    atomicAdd(h32 + c, 1u);
+                    const uint32_t old = atomicAdd(h32 + hk + c, ds);
+                    if (old + ds < old) atomicAdd(h32 + 2 * hk + c, 1u);
+                }
+            }
+            if (p.count) p.count[e] = (int32_t)c;
+            if (p.cn) p.cn[e] = est_f;
+            if (p.jac) {
+                const float fu = (float)cdu, fv = (float)cdv;
+                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
+                const float den = fu + fv - I;
+                p.jac[e] = den > 0.0f ? I / den : 0.0f;
+            }
+            if (p.S) atomicAdd(p.S + cv, est_d);
         }
+        if (p.S) add_u_runs(p.S, cu, V);
+        cu = nu;
+        cv = nv;
+        cdu = ndu;
+        cdv = ndv;
+    }
+
+    if (want_hist) {
+        __syncthreads();
+        if (KIND == BLOOM) {
+            for (int i = threadIdx.x; i < h32_len; i += blockDim.x)
+                if (h32[i]) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), (unsigned long long)h32[i]);
+        } else {
+            for (int i = threadIdx.x; i < hk; i += blockDim.x) {
+                if (h32[i]) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), (unsigned long long)h32[i]);
+                const unsigned long long d = (unsigned long long)h32[hk + i] | ((unsigned long long)h32[2 * hk + i] << 32);
+                if (d) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + hk + i), d);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 1-Hash pass: one warp per edge, kB edges per iteration (lane t < kB fetches
+// and owns edge t of the iteration).
+template <bool PAIRS>
+__global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
+    constexpr int kB = 4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *tab = reinterpret_cast<double *>(smem);
+    unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
+    float *tabF = reinterpret_cast<float *>(smem + 16 * (size_t)p.table_len);
+    uint32_t *h32 = reinterpret_cast<uint32_t *>(smem + 20 * (size_t)round_up4(p.table_len));
+    const uint32_t k = p.k;
+    const int hk = (int)k + 1, hk2 = hk * hk;
+    // counts [(k+1)^2], degree-sum low words and carries [(k+1)^2] each, then
+    // literal counts [k+1], literal degree-sum low words and carries [k+1] each
+    const int h32_len = 3 * hk2 + 3 * hk;
+    const bool want_hist = p.hist != nullptr;
+    {
+        const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
+        const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
+        for (int i = threadIdx.x; i < p.table_len; i += blockDim.x) {
+            tab[i] = p.table[i];
+            tabV[i] = gV[i];
+            tabF[i] = gF[i];
+        }
+    }
+    if (want_hist)
+        for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __syncthreads();
+
+    const unsigned lane = lane_id();
+    int64_t w0, w1;
+    warp_range<PAIRS>(p, w0, w1);
+    const int32_t iters = (int32_t)((w1 - w0 + kB - 1) / kB);
+    int32_t cu = -1, cv = -1, cdu = 0, cdv = 0;
+    if (lane < (unsigned)kB) item<PAIRS>(p, w0 + lane, w1, true, cu, cv, cdu, cdv);
+    unsigned long long acc_u = 0ull;  // fixed-point sum for acc_vertex
+    int32_t acc_vertex = -1;
+    for (int32_t it = 0; it < iters; ++it) {
+        const int64_t eb = w0 + (int64_t)it * kB;
+        int32_t us[kB], vs[kB], dus[kB], dvs[kB];
+        uint32_t su[kB], sv[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            us[t] = __shfl_sync(0xffffffffu, cu, t);
+            vs[t] = __shfl_sync(0xffffffffu, cv, t);
+            dus[t] = __shfl_sync(0xffffffffu, cdu, t);
+            dvs[t] = __shfl_sync(0xffffffffu, cdv, t);
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            su[t] = sv[t] = kEmpty;
+            if (us[t] >= 0 && lane < k) {
+                su[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)us[t] * p.stride) + lane);
+                sv[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)vs[t] * p.stride) + lane);
+            }
+        }
+        int32_t nu = -1, nv = -1, ndu = 0, ndv = 0;
+        if (lane < (unsigned)kB) item<PAIRS>(p, eb + kB + lane, w1, true, nu, nv, ndu, ndv);
+        int cnt_u = 0, K_u = 0, lit_u = 0;
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            int cu_, K_, lit_;
+            onehash_counts(su[t], sv[t], min((int)k, dus[t]), min((int)k, dvs[t]), (int)k, cu_, K_, lit_);
+            if ((int)lane == t) {
+                cnt_u = cu_;
+                K_u = K_;
+                lit_u = lit_;
+            }
+        }
+        // ---- epilogue: lane t owns edge t
+        const int64_t e = eb + lane;
+        if (lane < (unsigned)kB && cu == -2) {
+            if (p.count) p.count[e] = 0;
+            if (p.aux) p.aux[e] = 0;
+            if (p.cn) p.cn[e] = 0.0f;
+            if (p.jac) p.jac[e] = 0.0f;
+        }
+        if (lane < (unsigned)kB && cu >= 0) {
+            const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
+            const int ti = (p.est == PG_EST_1H_LITERAL) ? (int)k * hk + lit_u : K_u * hk + cnt_u;
+            const unsigned long long V = tabV[ti] * (unsigned long long)ds;
+            const float est_f = tabF[ti] * (float)ds;
+            if (want_hist) {
+                const int bin = K_u * hk + cnt_u;
+                atomicAdd(h32 + bin, 1u);
+                uint32_t old = atomicAdd(h32 + hk2 + bin, ds);
+                if (old + ds < old) atomicAdd(h32 + 2 * hk2 + bin, 1u);
+                atomicAdd(h32 + 3 * hk2 + lit_u, 1u);
+                old = atomicAdd(h32 + 3 * hk2 + hk + lit_u, ds);
+                if (old + ds < old) atomicAdd(h32 + 3 * hk2 + 2 * hk + lit_u, 1u);
+            }
+            if (p.aux) p.aux[e] = K_u | (lit_u << 16);
+            if (p.count) p.count[e] = (p.est == PG_EST_1H_LITERAL) ? lit_u : cnt_u;
+            if (p.cn) p.cn[e] = est_f;
+            if (p.jac) {
+                const float fu = (float)cdu, fv = (float)cdv;
+                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
+                const float den = fu + fv - I;
+                p.jac[e] = den > 0.0f ? I / den : 0.0f;
+            }
+            if (p.S) {
+                atomicAdd(p.S + cv, fx_to_f64(V));
+                if (PAIRS) {
+                    atomicAdd(p.S + cu, fx_to_f64(V));
+                } else {
+                    if (cu != acc_vertex) {
+                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
+                        acc_vertex = cu;
+                        acc_u = 0ull;
+                    }
+                    acc_u += V;
+                }
+            }
+        }
+        cu = nu;
+        cv = nv;
+        cdu = ndu;
+        cdv = ndv;
+    }
+    if (!PAIRS && p.S && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
+
+    if (want_hist) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < hk2; i += blockDim.x) {
+            if (h32[i]) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + i), (unsigned long long)h32[i]);
+            const unsigned long long d = (unsigned long long)h32[hk2 + i] | ((unsigned long long)h32[2 * hk2 + i] << 32);
+            if (d) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + hk2 + i), d);
+        }
+        for (int i = threadIdx.x; i < hk; i += blockDim.x) {
+            const uint32_t c = h32[3 * hk2 + i];
+            if (c) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + 2 * hk2 + i), (unsigned long long)c);
+            const unsigned long long d = (unsigned long long)h32[3 * hk2 + hk + i] |
+                                         ((unsigned long long)h32[3 * hk2 + 2 * hk + i] << 32);
+            if (d) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + 2 * hk2 + hk + i), d);
+        }
+    }
+}
+
+// Estimator tables (double, fixed point * 2^42, float): Bloom f(B1) for
+// B1 = 0..l; MinHash r(K, c) = c / (K + c) (the estimate is r * (d_u + d_v)).
+__global__ void k_table(double *tab, int32_t len, int32_t kind, int32_t est, uint32_t l, uint32_t b,
+                        uint32_t k) {
+    unsigned long long *tabV = reinterpret_cast<unsigned long long *>(tab + len);
+    float *tabF = reinterpret_cast<float *>(tab + 2 * len);
+    for (int32_t i = threadIdx.x; i < len; i += blockDim.x) {
+        double v;
+        if (kind == BLOOM) {
+            const uint32_t j = (uint32_t)i;
+            if (est == PG_EST_BF_L) {
+                v = (double)j / (double)b;
+            } else {
+                const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
+                v = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
+            }
+        } else {
+            const uint32_t hk = k + 1;
+            const uint32_t K = (kind == KHASH) ? k : (uint32_t)i / hk;
+            const uint32_t c = (uint32_t)i % hk;
+            v = (K + c) > 0 ? (double)c / (double)(K + c) : 0.0;
+        }
+        tab[i] = v;
+        tabV[i] = __double2ull_rn(ldexp(v, kFixBits));
+        tabF[i] = (float)v;
     }
 }
 
@@ -663,10 +800,11 @@ __global__ void k_lcc(const int32_t *__restrict__ row_ptr, int32_t n, double *S,
     if (tri) tri[v] = 0.5 * s;
 }
 
-template <int KIND, int L, int VPL, bool PAIRS>
-cudaError_t run(const Params &p, cudaStream_t s) {
-    const size_t smem = 8 * (size_t)p.table_len + (p.hist ? 8 * (size_t)p.hist_len : 0);
-    auto kern = k_intersect<KIND, L, VPL, PAIRS>;
+template <bool PAIRS>
+cudaError_t run_onehash(const Params &p, cudaStream_t s) {
+    const int hk = (int)p.k + 1;
+    const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)(3 * hk * hk + 3 * hk) : 0);
+    auto kern = k_onehash<PAIRS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -675,17 +813,34 @@ cudaError_t run(const Params &p, cudaStream_t s) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    const int grid = per_sm * device_info().sm_count;
-    kern<<<grid, kThreads, smem, s>>>(p);
+    kern<<<per_sm * device_info().sm_count, kThreads, smem, s>>>(p);
     note_launch();
     return cudaGetLastError();
 }
 
-template <int KIND, int L, int VPL, int B, bool PAIRS>
+template <int KIND, int L, int VPL, int B, int SB, bool UREUSE, int MINB, bool PAIRS>
 cudaError_t run_pass(const Params &p, cudaStream_t s) {
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
-    const size_t smem = 8 * (size_t)p.table_len + (p.hist ? 4 * (size_t)h32_len : 0);
-    auto kern = k_pass<KIND, L, VPL, B, PAIRS>;
+    const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)h32_len : 0);
+    auto kern = k_pass<KIND, L, VPL, B, SB, UREUSE, MINB, PAIRS>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<per_sm * device_info().sm_count, kThreads, smem, s>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
+cudaError_t run_lean(const Params &p, cudaStream_t s) {
+    const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
+    const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)h32_len : 0);
+    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -720,20 +875,26 @@ static int64_t table_len(int32_t kind, uint32_t l, uint32_t k) {
     return ((int64_t)k + 1) * (k + 1);
 }
 
-// The estimator table sits at the start of the intersect workspace.
+// The estimator tables sit at the start of the intersect workspace:
+// double [len] | uint64 [len] | float [len].
 size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k) {
-    return round_up(8 * (size_t)table_len(kind, l, k), 256);
+    return round_up(20 * (size_t)table_len(kind, l, k), 256);
 }
 
 cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int32_t n,
-                                const int32_t *upper_off, const int32_t *pairs, int64_t P,
+                                const EdgeIndex &ix, const int32_t *pairs, int64_t P,
                                 const pg_sketch &sk, int32_t estimator, const EdgeOutputs &out,
                                 double *table_ws, cudaStream_t s) {
     Params p{};
     p.row_ptr = row_ptr;
     p.col = col;
     p.n = n;
-    p.upper_off = upper_off;
+    p.upper_off = ix.upper_off;
+    p.eu = ix.eu;
+    p.ev = ix.ev;
+    p.edu = ix.edu;
+    p.edv = ix.edv;
+    p.cap = ix.cap;
     p.pairs = pairs;
     p.P = P;
     p.data = static_cast<const uint8_t *>(sk.data);
@@ -752,38 +913,54 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
     p.need_est = (out.S || out.cn || out.jac) ? 1 : 0;
     p.need_deg = (sk.kind != PG_SK_BLOOM || out.jac) ? 1 : 0;
-    k_table<<<1, 256, 0, s>>>(table_ws, sk.kind, estimator, sk.bits, sk.b, sk.k);
+    k_table<<<1, 256, 0, s>>>(table_ws, p.table_len, sk.kind, estimator, sk.bits, sk.b, sk.k);
     note_launch();
     const bool pr = pairs != nullptr;
     if (pr && P == 0) return cudaGetLastError();
+#define PG_LEAN(KIND, L, W, SB, UR, MB) \
+    if (!pr) return run_lean<KIND, L, W, SB, UR, MB>(p, s)
+#define PG_PASS(KIND, L, VPL, B, SB, UR, MB) \
+    return pr ? run_pass<KIND, L, VPL, B, SB, UR, MB, true>(p, s) : run_pass<KIND, L, VPL, B, SB, UR, MB, false>(p, s)
     if (sk.kind == PG_SK_BLOOM) {
-        // l <= 1024: at most 8 vectors, one per lane; B = min(L, 4) edges per group
+        // l <= 1024: at most 8 vectors, one per lane
         p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
-        const int L = pow2_at_least(p.nvec);
-        switch (L) {
-            case 1: return pr ? run_pass<BLOOM, 1, 1, 1, true>(p, s) : run_pass<BLOOM, 1, 1, 1, false>(p, s);
-            case 2: return pr ? run_pass<BLOOM, 2, 1, 2, true>(p, s) : run_pass<BLOOM, 2, 1, 2, false>(p, s);
-            case 4: return pr ? run_pass<BLOOM, 4, 1, 4, true>(p, s) : run_pass<BLOOM, 4, 1, 4, false>(p, s);
-            default: return pr ? run_pass<BLOOM, 8, 1, 4, true>(p, s) : run_pass<BLOOM, 8, 1, 4, false>(p, s);
+        switch (pow2_at_least(p.nvec)) {
+            case 1: PG_PASS(BLOOM, 1, 1, 1, 1, false, 4);
+            case 2:
+                if (sk.bits == 192) PG_LEAN(BLOOM, 2, 6, 2, true, 3);
+                if (sk.bits == 256) PG_LEAN(BLOOM, 2, 8, 2, true, 3);
+                PG_PASS(BLOOM, 2, 1, 2, 2, false, 4);
+            case 4:
+                if (sk.bits == 448) PG_LEAN(BLOOM, 4, 14, 4, true, 3);
+                if (sk.bits == 512) PG_LEAN(BLOOM, 4, 16, 4, true, 3);
+                PG_PASS(BLOOM, 4, 1, 4, 4, false, 4);
+            default:
+                if (sk.bits == 960) PG_LEAN(BLOOM, 8, 30, 2, true, 3);
+                if (sk.bits == 1024) PG_LEAN(BLOOM, 8, 32, 2, true, 3);
+                PG_PASS(BLOOM, 8, 1, 8, 4, false, 3);
         }
     } else if (sk.kind == PG_SK_KHASH) {
         // k <= 256: up to 64 vectors; at most 16 lanes with up to 4 vectors each
         p.nvec = (int32_t)((sk.k + 3) / 4);
+        if (sk.k == 64) PG_LEAN(KHASH, 16, 64, 8, true, 3);
+        if (sk.k == 32) PG_LEAN(KHASH, 8, 32, 2, true, 3);
+        if (sk.k == 16) PG_LEAN(KHASH, 4, 16, 4, true, 3);
         const int L = pow2_at_least(p.nvec) > 16 ? 16 : pow2_at_least(p.nvec);
-        if (L < 16) {
-            switch (L) {
-                case 1: return pr ? run_pass<KHASH, 1, 1, 1, true>(p, s) : run_pass<KHASH, 1, 1, 1, false>(p, s);
-                case 2: return pr ? run_pass<KHASH, 2, 1, 2, true>(p, s) : run_pass<KHASH, 2, 1, 2, false>(p, s);
-                case 4: return pr ? run_pass<KHASH, 4, 1, 4, true>(p, s) : run_pass<KHASH, 4, 1, 4, false>(p, s);
-                default: return pr ? run_pass<KHASH, 8, 1, 4, true>(p, s) : run_pass<KHASH, 8, 1, 4, false>(p, s);
-            }
+        switch (L) {
+            case 1: PG_PASS(KHASH, 1, 1, 1, 1, false, 4);
+            case 2: PG_PASS(KHASH, 2, 1, 2, 2, false, 4);
+            case 4: PG_PASS(KHASH, 4, 1, 4, 4, false, 4);
+            case 8: PG_PASS(KHASH, 8, 1, 4, 4, false, 4);
+            default:
+                if (p.nvec <= 16) PG_PASS(KHASH, 16, 1, 4, 4, false, 4);
+                if (p.nvec <= 32) PG_PASS(KHASH, 16, 2, 2, 2, false, 3);
+                PG_PASS(KHASH, 16, 4, 1, 1, false, 3);
         }
-        if (p.nvec <= 16) return pr ? run_pass<KHASH, 16, 1, 4, true>(p, s) : run_pass<KHASH, 16, 1, 4, false>(p, s);
-        if (p.nvec <= 32) return pr ? run_pass<KHASH, 16, 2, 2, true>(p, s) : run_pass<KHASH, 16, 2, 2, false>(p, s);
-        return pr ? run_pass<KHASH, 16, 4, 1, true>(p, s) : run_pass<KHASH, 16, 4, 1, false>(p, s);
+#undef PG_PASS
+#undef PG_LEAN
     } else {
         p.nvec = 0;
-        return pr ? run<ONEHASH, 32, 1, true>(p, s) : run<ONEHASH, 32, 1, false>(p, s);
+        return pr ? run_onehash<true>(p, s) : run_onehash<false>(p, s);
     }
 }
 

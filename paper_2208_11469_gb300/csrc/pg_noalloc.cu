@@ -95,7 +95,7 @@ extern "C" pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *inde
     launch_fill_u64(hist, bins, 0, stream);
     EdgeOutputs eo{};
     eo.hist = hist;
-    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, static_cast<const int32_t *>(index),
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, edge_index_view(index, g->n, g->nnz),
                                     nullptr, 0, *sk, estimator, eo, tab, stream),
                 "pg_triangle_count_noalloc");
     PG_TRY_CUDA(launch_tc_finalize(hist, *sk, estimator, out, stream), "pg_triangle_count_noalloc");

@@ -84,7 +84,7 @@ def lib() -> ctypes.CDLL:
                 "pg_last_error": (ctypes.c_char_p, []),
                 "pg_version": (i32, []),
                 "pg_validate_csr": (i32, [P(Csr), i32, vp, vp]),
-                "pg_edge_index_bytes": (sz, [i32]),
+                "pg_edge_index_bytes": (sz, [i32, i64]),
                 "pg_build_edge_index": (i32, [P(Csr), vp, sz, vp]),
                 "pg_edge_index_upper_off": (vp, [vp]),
                 "pg_sketch_stride": (i64, [i32, u32, u32]),
@@ -180,7 +180,7 @@ def graph(row_ptr: torch.Tensor, col: torch.Tensor, build_index: bool = True) ->
 
 def build_edge_index(g: Graph) -> torch.Tensor:
     L = lib()
-    nbytes = L.pg_edge_index_bytes(g.n)
+    nbytes = L.pg_edge_index_bytes(g.n, g.nnz)
     idx = _dev_bytes(nbytes, g.device)
     c = g.csr()
     _check(L.pg_build_edge_index(ctypes.byref(c), _ptr(idx), idx.numel(), _stream()), "pg_build_edge_index")

@@ -58,7 +58,8 @@ def test_sizing_helpers(L):
     assert pg.bloom_bits_for_budget(0.25, n, nnz) == 448
     assert pg.bloom_bits_for_budget(0.50, n, nnz) == 960
     assert pg.bloom_bits_for_budget(0.25, 4096, 65536) == 128  # 136 bits -> one 64-bit word less
-    assert L.pg_edge_index_bytes(0) > 0
+    assert L.pg_edge_index_bytes(0, 0) > 0
+    assert L.pg_edge_index_bytes(10, 100) >= 4 * 11 + 8 * 50
 
 
 def _csr(n=4, nnz=6, rp=0x1000, col=0x2000):
