@@ -504,7 +504,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR and sketch tables >> 129 MB), no flush",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": per,
-            "roofline": {"bound": "hbm", "kernel": f"k_intersect ({dom} pass, pg_analyze)", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": f"k_lean ({dom} pass of pg_analyze)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes": alg, "peak_source": peak_kind},
             "e2e": e2e,
