@@ -1,6 +1,7 @@
 """Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat24|rmat24_b50|rmat20|er4096]
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096]
                     [--impl ours|reference]
 
 A step is one pass of the whole sketched path over the synthetic graph of the
@@ -48,6 +49,10 @@ WORKLOADS = {
     "rmat20": dict(gen=("rmat", 20, 16, 20), budget=0.25, b=2, khash=None, onehash=32, jaccard=True),
     # Erdos-Renyi n = 4096, average degree 16, Bloom 256 bits b = 2, k-Hash k = 16
     "er4096": dict(gen=("er", 4096, 16.0, 1), bits=256, b=2, khash=16, onehash=None, jaccard=False),
+    # 4096 graphs (half Erdos-Renyi, half R-MAT), n log-uniform in [2^8, 2^16], average degree
+    # lognormal (median 12, clipped to 4..64); per-graph Bloom length and hash count from the
+    # autotuner at 25% of each graph's CSR bytes; one captured batch run against one launch per graph
+    "batch4096": dict(batch=4096, budget=0.25, seed=1),
 }
 
 
@@ -79,6 +84,8 @@ def barrier(ws):
 
 def generate(workload: str, device):
     from paper_2208_11469_gb300 import synth
+    if "batch" in WORKLOADS[workload]:
+        return generate_batch(workload, device)
     kind, *a = WORKLOADS[workload]["gen"]
     if kind == "rmat":
         scale, ef, seed = a
@@ -394,12 +401,221 @@ def oracle_sample(row_ptr_d, col_d, pipe_cfg, bits, target_s=15.0, seed=0):
     return npass * e / dt, dt, e, desc
 
 
+# ------------------------------------------------------------ batching
+def generate_batch(workload: str, device):
+    """The graph mix, its autotuned Bloom parameters, and the graphs ordered
+    by (bits, b) and concatenated block-diagonally. Returns (parts, cfg,
+    row_ptr, col, voff) with parts and cfg in batch order."""
+    from paper_2208_11469_gb300 import pg, synth
+    w = WORKLOADS[workload]
+    parts = synth.batch_mix(w["batch"], seed=w["seed"], device=device)
+    n = np.array([int(rp.numel()) - 1 for rp, _ in parts], dtype=np.int32)
+    nnz = np.array([int(cl.numel()) for _, cl in parts], dtype=np.int64)
+    cfg = pg.batch_autotune(n, nnz, w["budget"])
+    order = sorted(range(len(parts)), key=lambda i: (cfg[i], i))
+    parts = [parts[i] for i in order]
+    cfg = [cfg[i] for i in order]
+    rp, cl, voff = synth.block_diagonal(parts)
+    return parts, cfg, rp, cl, voff
+
+
+def oracle_batch_sample(parts, cfg, target_s=15.0, seed=0):
+    """The oracle over whole graphs of the mix, drawn at random until about
+    target_s seconds of work: sketches, pass and totals of each graph."""
+    from oracle import oracle as O
+    gen = np.random.default_rng(seed)
+    order = gen.permutation(len(parts))
+    edges, secs, graphs = 0, 0.0, 0
+    for i in order:
+        rp = parts[i][0].cpu().numpy()
+        cl = parts[i][1].cpu().numpy()
+        t0 = time.perf_counter()
+        r = O.analyze(rp, cl, O.EST_BF_AND, l=cfg[i][0], b=cfg[i][1], seed=1)
+        secs += time.perf_counter() - t0
+        edges += r["m"]
+        graphs += 1
+        if secs >= target_s:
+            break
+    desc = (f"{graphs} whole graphs of the mix drawn at random ({edges} upper edges): oracle Bloom sketches, "
+            f"AND estimates, triangle count and LCC, serial C/numpy on 1 host core")
+    return edges / secs, secs, edges, desc
+
+
+def run_batch(args, ws, rank, dev):
+    from paper_2208_11469_gb300 import pg
+    parts, cfg, rp, cl, voff = generate_batch(args.workload, dev)
+    G = len(parts)
+    g = pg.graph(rp, cl, build_index=False)
+    batch = pg.Batch(g, voff, cfg, seed=1, want_tri=False)
+    m = int(sum(int((p[0][1:] - p[0][:-1]).sum()) // 2 for p in parts))
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    launches0 = pg.kernel_launches()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            batch.run()
+        stream.synchronize()
+        launches_w = pg.kernel_launches()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev.index or 0) as clk:
+            barrier(ws)
+            torch.cuda.synchronize()
+            start.record(stream)
+            for _ in range(args.steps):
+                batch.run()
+            end.record(stream)
+            torch.cuda.synchronize()
+            barrier(ws)
+    graph_launches = pg.kernel_launches() - launches_w
+    ms = start.elapsed_time(end) / args.steps
+    ms_max = max_over_ranks(ms, ws, dev)
+    value = m * ws / (ms_max * 1e-3)
+    res = batch.results()
+    # kernels inside one captured run: count them on one eager run
+    l0 = pg.kernel_launches()
+    batch.run(stream=0)
+    torch.cuda.synchronize()
+    kernels_per_run = pg.kernel_launches() - l0
+
+    # the same work as one launch sequence per graph
+    singles = []
+    build_ws = torch.empty(max(max(pg.build_workspace_bytes(pg.graph(p[0], p[1], build_index=False))
+                                   for p in parts), 16), dtype=torch.uint8, device=dev)
+    for (prp, pcl), (bits, b) in zip(parts, cfg):
+        gi = pg.graph(prp, pcl, build_index=True)
+        sk = pg.alloc_sketch(gi, pg.SK_BLOOM, bits=bits, b=b, seed=1)
+        singles.append((gi, sk, pg.workspace(gi, sk, pg.EST_BF_AND), pg.tc_result_buffer(dev),
+                        torch.empty(gi.n, dtype=torch.float32, device=dev)))
+
+    def per_graph_step():
+        for gi, sk, wsi, tc, lcc in singles:
+            pg.build_edge_index_into(gi)
+            pg.build_bloom(gi, sk.bits, sk.b, sk.seed, out=sk, workspace=build_ws)
+            pg.analyze(gi, sk, pg.EST_BF_AND, ws=wsi, tc=tc, lcc=lcc)
+
+    per_graph_step()
+    torch.cuda.synchronize()
+    pl0 = pg.kernel_launches()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    a.record()
+    per_steps = 2
+    for _ in range(per_steps):
+        per_graph_step()
+    b_.record()
+    torch.cuda.synchronize()
+    per_ms = a.elapsed_time(b_) / per_steps
+    per_wall = (time.perf_counter() - t0) * 1e3 / per_steps
+    per_launches = (pg.kernel_launches() - pl0) // per_steps
+    mismatch = 0
+    for (gi, sk, wsi, tc, lcc), r in zip(singles, res):
+        s1 = pg.read_tc_result(tc)
+        mismatch += int(s1["count_sum"] != r["count_sum"] or s1["edges"] != r["edges"])
+    del singles
+
+    # exact GPU intersection on the union graph: per-vertex triangles -> per-graph counts
+    exact = None
+    if not args.no_exact:
+        gx = pg.graph(rp, cl, build_index=True)
+        wsx = pg.workspace(gx, None, pg.EST_EXACT)
+        pg.clustering(gx, None, pg.EST_EXACT, ws=wsx)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        _, tri, _ = pg.clustering(gx, None, pg.EST_EXACT, ws=wsx)
+        eb.record()
+        torch.cuda.synchronize()
+        seg = torch.repeat_interleave(torch.arange(G, device=dev),
+                                      torch.from_numpy(np.diff(voff)).to(dev))
+        tc_exact = torch.zeros(G, dtype=torch.float64, device=dev).index_add_(0, seg, tri) / 3.0
+        tc_exact = tc_exact.cpu().numpy()
+        est = np.array([r["est_tc"] for r in res])
+        ok = tc_exact > 0
+        rel = np.abs(est[ok] - tc_exact[ok]) / tc_exact[ok]
+        exact = {"ms": ea.elapsed_time(eb), "edges_per_s": m / (ea.elapsed_time(eb) * 1e-3),
+                 "tc_rel_error_median": float(np.median(rel)) if rel.size else None,
+                 "tc_rel_error_p90": float(np.quantile(rel, 0.9)) if rel.size else None,
+                 "tc_rel_error_total": float((est.sum() - tc_exact.sum()) / tc_exact.sum())}
+        del gx, wsx
+
+    # end to end: the union CSR from pinned host memory, results back to the host
+    e2e = None
+    if args.e2e_steps > 0:
+        host_rp, host_cl = rp.cpu().pin_memory(), cl.cpu().pin_memory()
+        h_tc = torch.empty(batch.tc.shape, dtype=torch.uint8, pin_memory=True)
+        h_lcc = torch.empty(batch.lcc.shape, dtype=torch.float32, pin_memory=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            for _ in range(args.e2e_steps):
+                g.row_ptr.copy_(host_rp, non_blocking=True)
+                g.col.copy_(host_cl, non_blocking=True)
+                batch.run()
+                h_tc.copy_(batch.tc, non_blocking=True)
+                h_lcc.copy_(batch.lcc, non_blocking=True)
+            eb.record(stream)
+            stream.synchronize()
+        e_ms = max_over_ranks(ea.elapsed_time(eb) / args.e2e_steps, ws, dev)
+        e2e = {"value": m * ws / (e_ms * 1e-3), "unit": "intersections/s",
+               "h2d_bytes_per_step": 4 * (host_rp.numel() + host_cl.numel()),
+               "d2h_bytes_per_step": h_tc.numel() + 4 * h_lcc.numel(), "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, e, desc = oracle_batch_sample(parts, cfg, target_s=15.0)
+        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    # roofline of the captured run as a whole: algorithmic bytes of the index, the builds and the pass
+    n_tot, nnz_tot = g.n, g.nnz
+    strides = {c: pg.sketch_stride(pg.SK_BLOOM, c[0], 0) for c in set(cfg)}
+    sketch_bytes = sum((int(p[0].numel()) - 1) * strides[c] for p, c in zip(parts, cfg))
+    pass_bytes = sum(int(cl_.numel()) // 2 * (c[0] / 8 + 4) + (int(rp_.numel()) - 1) * (c[0] / 8 + 24)
+                     for (rp_, cl_), c in zip(parts, cfg))
+    index_bytes = 4 * (n_tot + 1) + 4 * nnz_tot + 16 * m + 4 * n_tot
+    build_bytes = 4 * (n_tot + 1) + 4 * nnz_tot + sketch_bytes
+    alg = index_bytes + build_bytes + pass_bytes
+    peak, peak_kind = peaks()
+    achieved = alg / (ms_max * 1e-3) / 1e9
+    buckets = {}
+    for c, v in zip(cfg, batch.variants):
+        buckets.setdefault(f"{c[0]}b{c[1]}", {"graphs": 0, "lanes": v})["graphs"] += 1
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded on-device generator)",
+            "config": {"workload": args.workload, "graphs": G, "n": n_tot, "nnz": nnz_tot, "m": m,
+                       "budget": WORKLOADS[args.workload]["budget"], "buckets": buckets,
+                       "l2": "inputs larger than L2 (union CSR and sketches >> 129 MB), no flush",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "pg_batch_run (whole captured run: index, builds, passes)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "e2e": e2e,
+            "gpu_launches": kernels_per_run * args.steps,
+            "kernels_per_run": kernels_per_run,
+            "cuda_graph_launches": graph_launches,
+            "clocks": clk.summary(),
+            "per_graph_launches": {"ms_per_step": per_ms, "wall_ms_per_step": per_wall,
+                                   "value": m / (per_ms * 1e-3), "kernels_per_step": per_launches,
+                                   "speedup_of_batch": per_ms / ms, "integer_mismatches": mismatch},
+            "exact_gpu": exact,
+            "results": {"est_tc_sum": float(sum(r["est_tc"] for r in res)),
+                        "count_sum": int(sum(r["count_sum"] for r in res))},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     cfg = WORKLOADS[args.workload]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
+    if "batch" in cfg:
+        return run_reference_batch(args, ws, dev)
     rp, cl = generate(args.workload, dev)
     bits = cfg.get("bits") or budget_bits(cfg["budget"], rp.numel() - 1, cl.numel())
     per_step = 4.0 * max(1, 60 // max(args.steps + args.warmup, 1))
@@ -415,6 +631,27 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
             "data": "synthetic", "config": {"workload": args.workload, "bloom_bits": bits},
+            "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_batch(args, ws, dev):
+    parts, cfg, _, _, _ = generate_batch(args.workload, dev)
+    per_step = 4.0 * max(1, 60 // max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_batch_sample(parts, cfg, target_s=min(per_step, 5.0), seed=1)
+    rates, secs, desc = [], 0.0, ""
+    for i in range(args.steps):
+        r, dt, e, desc = oracle_batch_sample(parts, cfg, target_s=per_step, seed=100 + i)
+        rates.append(r)
+        secs += dt
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
+            "data": "synthetic", "config": {"workload": args.workload, "graphs": len(parts)},
             "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -448,6 +685,11 @@ def main():
     from paper_2208_11469_gb300 import pg
 
     dev = torch.device("cuda", local)
+    if "batch" in WORKLOADS[args.workload]:
+        run_batch(args, ws, rank, dev)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     rp, cl = generate(args.workload, dev)
     pipe = Pipeline(args.workload, rp, cl)
     torch.cuda.synchronize()

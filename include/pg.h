@@ -282,6 +282,69 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
 pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *index, const pg_sketch *sk,
                                     int32_t estimator, pg_tc_result *out, pg_stream_t stream);
 
+/* ---------------------------------------------------------------- batch --
+ * Many small graphs analysed together (the per-graph Bloom-filter triangle
+ * count of Sec. V, Eq. bf_int, and the LCC of Sec. II-B, per graph), in one
+ * launch sequence that is captured once as a CUDA graph and replayed.
+ *
+ * The G graphs come as ONE block-diagonal CSR g with global vertex ids: graph
+ * i owns vertices [voff[i], voff[i+1]) and its rows only name vertices of the
+ * same range (voff: HOST int32 [G+1], voff[0] = 0, voff[G] = g->n). Each
+ * graph's sketch hashes its own ids (global id - voff[i]), so a graph's
+ * sketch and estimates are the same in the batch and alone.
+ *
+ * Per graph i, cfg[i] sets the Bloom filter: bits in {64, 128, 256, 512,
+ * 1024}, b in [1, 16], and variant = lanes per sketch row of the pass (0 =
+ * let pg_batch_create time the candidates and choose; it writes the choice
+ * back into cfg). Graphs with equal (bits, b) must be contiguous: order them
+ * by bucket. */
+typedef struct pg_batch_config {
+    uint32_t bits;
+    uint32_t b;
+    int32_t variant;
+    int32_t reserved;
+} pg_batch_config;
+typedef struct pg_batch pg_batch;
+
+/* Autotuner, host only: cfg[i].bits = the largest power of two in [64, 1024]
+ * not above budget * (CSR bytes of graph i) * 8 / n_i (the storage budget s
+ * of Sec. V-A), cfg[i].b = the b in {1, 2, 4} with the smallest modelled
+ * error of the AND estimator at that length (bias at the expected popcount
+ * plus the MSE bound of Prop. 4.1, for neighbourhoods of the graph's average
+ * degree sharing a tenth of their elements), cfg[i].variant = 0.
+ * n, nnz: HOST arrays [graphs]. */
+pg_status pg_batch_autotune(const int32_t *n, const int64_t *nnz, int32_t graphs, double budget,
+                            pg_batch_config *cfg);
+
+/* Device workspace a batch needs (edge index, graph tables, per-graph
+ * histograms, sketches, per-vertex sums); 0 for invalid arguments. */
+size_t pg_batch_workspace_bytes(const pg_csr *g, int32_t graphs, const int32_t *voff,
+                                const pg_batch_config *cfg);
+
+/* Create a batch over g (DEVICE CSR, resident for the batch's lifetime) and
+ * a caller workspace of pg_batch_workspace_bytes. Outputs (DEVICE, written by
+ * every pg_batch_run): tc pg_tc_result [G] (graph i's triangle count and
+ * edge totals, as pg_triangle_count with PG_EST_BF_AND), lcc float [n] and
+ * tri double [n] or NULL (per vertex, as pg_clustering). Synchronises the
+ * stream; when a variant is 0 it runs and times the candidate passes once.
+ * Errors: PG_ERR_INVALID_ARG (NULLs, voff not covering g, non-contiguous
+ * buckets, b out of range), PG_ERR_UNSUPPORTED (bits), PG_ERR_NO_MEMORY
+ * (workspace too small), PG_ERR_CUDA. On error *out is unchanged. */
+pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff, pg_batch_config *cfg,
+                          uint32_t seed, void *workspace, size_t workspace_bytes, pg_tc_result *tc,
+                          float *lcc, double *tri, pg_stream_t stream, pg_batch **out);
+
+/* One run: edge index, sketches and pass of every graph, then LCC and the
+ * per-graph triangle counts. On a non-default stream the first run captures
+ * the sequence as a CUDA graph (for that stream) and every run launches it;
+ * on the default stream (NULL) the kernels are launched one by one. The CSR
+ * contents may change between runs (same n, nnz and voff). Asynchronous. */
+pg_status pg_batch_run(pg_batch *batch, pg_stream_t stream);
+
+/* Free the host state and the captured graph (not the workspace). NULL is a
+ * no-op. */
+pg_status pg_batch_destroy(pg_batch *batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -97,11 +97,22 @@ cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32
 cudaError_t launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
                             int check_symmetry, int64_t *result, cudaStream_t s);
 
+// Per-vertex parameters of batched graphs (pg_batch.cu): global vertex of local
+// vertex v = v_base + v, its graph gid[.], the graph's first global id voff[g]
+// and hash count b_of[g]. gid == nullptr: a single graph.
+struct BatchMap {
+    const int32_t *gid;
+    const int32_t *voff;
+    const uint8_t *b_of;
+    int64_t v_base;
+};
+
 // Defined in pg_sketch.cu. hub_base: build workspace (build_workspace_bytes).
 size_t build_workspace_bytes(int64_t nnz);
 cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32_t n,
                                uint32_t l, uint32_t b, uint32_t seed, uint8_t *data,
-                               int64_t stride, int32_t *hub_base, cudaStream_t s);
+                               int64_t stride, int32_t *hub_base, cudaStream_t s,
+                               const BatchMap *bmap = nullptr);
 cudaError_t launch_build_khash(const int32_t *row_ptr, const int32_t *col, int32_t n, uint32_t k,
                                uint32_t seed, uint8_t *data, int64_t stride, int32_t *hub_base,
                                cudaStream_t s);
@@ -128,6 +139,17 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
                                 double *table_ws, cudaStream_t s);
 cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,
                                pg_tc_result *out, cudaStream_t s);
+// Batch (pg_batch.cu): the Bloom pass over the upper edges of vertices
+// [v_lo, v_hi) of a block-diagonal union graph, with per-graph histograms at
+// hist + hoff[gid[u]]; variant = lanes per row (batch_variants lists them).
+cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_t n, const EdgeIndex &ix,
+                              const pg_sketch &sk, int32_t estimator, int32_t variant, const int32_t *gid,
+                              const int64_t *hoff, int32_t v_lo, int32_t v_hi, uint64_t *hist, double *S,
+                              double *table_ws, cudaStream_t s);
+int32_t batch_variants(uint32_t bits, int32_t *out);
+cudaError_t launch_batch_finalize(const uint64_t *hist, const int64_t *hoff, const uint32_t *bits_of,
+                                  const uint8_t *b_of, int32_t graphs, int32_t estimator, pg_tc_result *out,
+                                  cudaStream_t s);
 cudaError_t launch_lcc_finalize(const int32_t *row_ptr, int32_t n, double *S, float *lcc,
                                 double *tri, cudaStream_t s);
 

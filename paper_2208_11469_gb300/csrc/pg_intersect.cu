@@ -41,6 +41,9 @@ struct Params {
     int64_t cap;            // list capacity
     const int32_t *pairs;   // pair list (pair source)
     int64_t P;
+    const int32_t *gid;     // batch: graph of each vertex (null: single graph)
+    const int64_t *hoff;    // batch: offset of each graph's histogram in hist
+    int32_t v_lo, v_hi;     // batch: this launch covers the upper edges of vertices [v_lo, v_hi)
     const uint8_t *data;
     int64_t stride;
     int32_t nvec;       // 16-byte vectors per row that carry payload
@@ -177,15 +180,20 @@ template <bool PAIRS>
 __device__ __forceinline__ void warp_range(const Params &p, int64_t &w0, int64_t &w1) {
     const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
-    int64_t total;
+    int64_t lo = 0, hi;
     if (PAIRS) {
-        total = p.P;
+        hi = p.P;
+    } else if (p.gid) {
+        lo = p.upper_off[p.v_lo];
+        hi = p.upper_off[p.v_hi];
+        if (lo > p.cap) lo = p.cap;
+        if (hi > p.cap) hi = p.cap;
     } else {
-        total = p.upper_off[p.n];
-        if (total > p.cap) total = p.cap;
+        hi = p.upper_off[p.n];
+        if (hi > p.cap) hi = p.cap;
     }
-    w0 = warp * total / warps;
-    w1 = (warp + 1) * total / warps;
+    w0 = lo + warp * (hi - lo) / warps;
+    w1 = lo + (warp + 1) * (hi - lo) / warps;
 }
 
 // (u, v) of work item e (u = -1: beyond the range; -2: pair with an id outside
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
 // The row of u stays in registers while u repeats (u is non-decreasing along
 // the list); the epilogue is the same as in k_pass, run by every lane for its
 // own item.
-template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool BATCH>
 __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     // W: 32-bit words of the row payload (l / 32 for Bloom, k for k-Hash)
     constexpr int NV = (W + 3) / 4;  // vectors per row
@@ -419,6 +427,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const int hk = (int)p.k + 1;
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * hk;
     const bool want_hist = p.hist != nullptr;
+    constexpr bool batch = BATCH;  // per-graph histograms of a batch bucket (p.gid, p.hoff)
     {
         const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
         const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
@@ -428,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             tabF[i] = gF[i];
         }
     }
-    if (want_hist)
+    if (want_hist && !batch)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
     __syncthreads();
 
@@ -443,6 +452,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const uint32_t grp_shift = (uint32_t)grp * 16u;
     const bool need_deg = p.need_deg != 0;
     const uint8_t *rowbase = p.data + 16 * vidx;
+    // sketch rows this launch may read: a batch launch holds only its bucket's rows
+    const int32_t row_lo = batch ? p.v_lo : 0;
+    const int32_t row_hi = batch ? p.v_hi - 1 : 0;
 
     int64_t w0, w1;
     warp_range<false>(p, w0, w1);
@@ -466,12 +478,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             for (int t = 0; t < SB; ++t) {
                 const unsigned src = (unsigned)(grp * L + s0 + t);  // lane owning this step's item
                 us[t] = __shfl_sync(0xffffffffu, cu, src);
-                const int32_t vt = max(__shfl_sync(0xffffffffu, cv, src), 0);  // past the range: row 0, unused
+                // rows outside [row_lo, row_hi] (past the range, or a batch graph naming another
+                // graph's vertex) read a row of this launch's sketch table and count nothing useful
+                const int32_t vs_ = max(__shfl_sync(0xffffffffu, cv, src), row_lo);
+                const int32_t vt = batch ? min(vs_, row_hi) : vs_;
                 rb[t] = ldg4(rowbase + (int64_t)vt * p.stride);
                 if (UREUSE && us[t] == cur_u)
                     ra[t] = cur_row;
                 else
-                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], 0) * p.stride);
+                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], row_lo) * p.stride);
             }
 #pragma unroll
             for (int t = 0; t < SB; ++t) {
@@ -512,7 +527,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
                     est_d = tab[c];
                     est_f = tabF[c];
                 }
-                if (want_hist) atomicAdd(h32 + c, 1u);
+                if (want_hist && !batch) atomicAdd(h32 + c, 1u);
             } else {
                 const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
                 if (p.need_est) {
@@ -537,13 +552,22 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             if (p.S) atomicAdd(p.S + cv, est_d);
         }
         if (p.S) add_u_runs(p.S, cu, V);
+        if (batch && want_hist) {
+            // per-graph histograms in global memory; lanes with the same (graph, count) add once
+            const int32_t gg = cu >= 0 ? __ldg(p.gid + cu) : -1;
+            const uint32_t key = cu >= 0 ? (uint32_t)gg * 2048u + c : 0xFFFFFFFFu;
+            const unsigned same = __match_any_sync(0xffffffffu, key);
+            if (cu >= 0 && (int)lane == __ffs(same) - 1)
+                atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + __ldg(p.hoff + gg) + c),
+                          (unsigned long long)__popc(same));
+        }
         cu = nu;
         cv = nv;
         cdu = ndu;
         cdv = ndv;
     }
 
-    if (want_hist) {
+    if (want_hist && !batch) {
         __syncthreads();
         if (KIND == BLOOM) {
             for (int i = threadIdx.x; i < h32_len; i += blockDim.x)
@@ -725,11 +749,10 @@ __global__ void k_table(double *tab, int32_t len, int32_t kind, int32_t est, uin
     }
 }
 
-// Graph totals from the histograms in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_tc_finalize(const uint64_t *__restrict__ hist,
-                                                     int32_t kind, int32_t est, uint32_t l,
-                                                     uint32_t b, uint32_t k,
-                                                     pg_tc_result *out) {
+// Graph totals from the histograms in a fixed order (deterministic): one
+// 256-thread block reduces one histogram.
+__device__ __forceinline__ void tc_dot_block(const uint64_t *__restrict__ hist, int32_t kind, int32_t est,
+                                             uint32_t l, uint32_t b, uint32_t k, pg_tc_result *out) {
     __shared__ double s_main[256], s_alt[256];
     __shared__ unsigned long long s_edges[256], s_sum[256];
     double main_ = 0.0, alt = 0.0;
@@ -790,6 +813,22 @@ __global__ void __launch_bounds__(256) k_tc_finalize(const uint64_t *__restrict_
     }
 }
 
+__global__ void __launch_bounds__(256) k_tc_finalize(const uint64_t *__restrict__ hist, int32_t kind,
+                                                     int32_t est, uint32_t l, uint32_t b, uint32_t k,
+                                                     pg_tc_result *out) {
+    tc_dot_block(hist, kind, est, l, b, k, out);
+}
+
+// Batch: block g reduces graph g's Bloom histogram with the graph's own l and b.
+__global__ void __launch_bounds__(256) k_batch_tc_finalize(const uint64_t *__restrict__ hist,
+                                                           const int64_t *__restrict__ hoff,
+                                                           const uint32_t *__restrict__ bits_of,
+                                                           const uint8_t *__restrict__ b_of, int32_t est,
+                                                           pg_tc_result *out) {
+    const int g = blockIdx.x;
+    tc_dot_block(hist + hoff[g], BLOOM, est, bits_of[g], b_of[g], 0, out + g);
+}
+
 __global__ void k_lcc(const int32_t *__restrict__ row_ptr, int32_t n, double *S, float *lcc,
                       double *tri) {
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -836,11 +875,11 @@ cudaError_t run_pass(const Params &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool BATCH = false>
 cudaError_t run_lean(const Params &p, cudaStream_t s) {
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
     const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)h32_len : 0);
-    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB>;
+    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB, BATCH>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -962,6 +1001,70 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
         p.nvec = 0;
         return pr ? run_onehash<true>(p, s) : run_onehash<false>(p, s);
     }
+}
+
+cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_t n, const EdgeIndex &ix,
+                              const pg_sketch &sk, int32_t estimator, int32_t variant, const int32_t *gid,
+                              const int64_t *hoff, int32_t v_lo, int32_t v_hi, uint64_t *hist, double *S,
+                              double *table_ws, cudaStream_t s) {
+    Params p{};
+    p.row_ptr = row_ptr;
+    p.col = col;
+    p.n = n;
+    p.upper_off = ix.upper_off;
+    p.eu = ix.eu;
+    p.ev = ix.ev;
+    p.edu = ix.edu;
+    p.edv = ix.edv;
+    p.cap = ix.cap;
+    p.data = static_cast<const uint8_t *>(sk.data);
+    p.stride = sk.stride_bytes;
+    p.l = sk.bits;
+    p.k = sk.k;
+    p.est = estimator;
+    p.S = S;
+    p.hist = hist;
+    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k);
+    p.table = table_ws;
+    p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
+    p.need_est = S ? 1 : 0;
+    p.need_deg = 0;
+    p.gid = gid;
+    p.hoff = hoff;
+    p.v_lo = v_lo;
+    p.v_hi = v_hi;
+    p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
+    k_table<<<1, 256, 0, s>>>(table_ws, p.table_len, sk.kind, estimator, sk.bits, sk.b, sk.k);
+    note_launch();
+    // variant: lanes per row (the autotuner times the candidates of each width)
+    switch (sk.bits) {
+        case 64: return variant == 2 ? run_lean<BLOOM, 2, 2, 2, true, 3, true>(p, s) : run_lean<BLOOM, 1, 2, 1, true, 4, true>(p, s);
+        case 128: return variant == 2 ? run_lean<BLOOM, 2, 4, 2, true, 3, true>(p, s) : run_lean<BLOOM, 1, 4, 1, true, 4, true>(p, s);
+        case 256: return variant == 4 ? run_lean<BLOOM, 4, 8, 4, true, 3, true>(p, s) : run_lean<BLOOM, 2, 8, 2, true, 3, true>(p, s);
+        case 512: return variant == 8 ? run_lean<BLOOM, 8, 16, 2, true, 3, true>(p, s) : run_lean<BLOOM, 4, 16, 4, true, 3, true>(p, s);
+        case 1024: return run_lean<BLOOM, 8, 32, 2, true, 3, true>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int32_t batch_variants(uint32_t bits, int32_t *out) {
+    switch (bits) {
+        case 64: out[0] = 1; out[1] = 2; return 2;
+        case 128: out[0] = 1; out[1] = 2; return 2;
+        case 256: out[0] = 2; out[1] = 4; return 2;
+        case 512: out[0] = 4; out[1] = 8; return 2;
+        case 1024: out[0] = 8; return 1;
+        default: return 0;
+    }
+}
+
+cudaError_t launch_batch_finalize(const uint64_t *hist, const int64_t *hoff, const uint32_t *bits_of,
+                                  const uint8_t *b_of, int32_t graphs, int32_t estimator, pg_tc_result *out,
+                                  cudaStream_t s) {
+    if (graphs <= 0) return cudaSuccess;
+    k_batch_tc_finalize<<<graphs, 256, 0, s>>>(hist, hoff, bits_of, b_of, estimator, out);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,

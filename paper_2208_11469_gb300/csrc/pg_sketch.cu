@@ -57,6 +57,18 @@ __device__ __forceinline__ int hub_find(const int2 *rec, int count, int64_t t) {
     return lo;
 }
 
+// Batched graphs (pg_batch_*): vertex v of this launch is global vertex
+// bm.v_base + v; its graph g = gid[.] sets its hash count b_of[g] and the id
+// offset voff[g] that turns global neighbour ids back into the graph's own ids
+// (so a graph's sketch is the same alone and in a batch).
+__device__ __forceinline__ void vertex_params(const BatchMap &bm, int64_t v, uint32_t &b, int32_t &id0) {
+    if (bm.gid) {
+        const int32_t g = __ldg(bm.gid + bm.v_base + v);
+        b = bm.b_of[g];
+        id0 = __ldg(bm.voff + g);
+    }
+}
+
 // ---------------------------------------------------------------- Bloom --
 // Warp-private filter in shared memory (32-bit words); lanes set bits with
 // shared atomicOr, then the warp stores the row with coalesced 8-byte stores.
@@ -64,7 +76,7 @@ template <int kMaxWords32>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n, uint32_t l,
     uint32_t b, uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t hub_threshold,
-    int32_t chunk, int32_t *hub_base) {
+    int32_t chunk, int32_t *hub_base, BatchMap bm) {
     __shared__ uint32_t filt[kBuildThreads / 32][kMaxWords32];
     __shared__ uint32_t pre_s[16];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
@@ -76,15 +88,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     const int64_t warps_total = (int64_t)gridDim.x * (kBuildThreads / 32);
     for (int64_t v = blockIdx.x * (int64_t)(kBuildThreads / 32) + warp; v < n; v += warps_total) {
         const int32_t a = row_ptr[v], e = row_ptr[v + 1];
+        uint32_t bv = b;
+        int32_t id0 = 0;
+        vertex_params(bm, v, bv, id0);
         for (int t = lane; t < words32; t += 32) f[t] = 0u;
         __syncwarp();
         if (e - a > hub_threshold) {
             if (lane == 0) hub_append(hubs, (int32_t)v, (e - a + chunk - 1) / chunk);
         } else {
             for (int32_t j = a + lane; j < e; j += 32) {
-                const uint32_t px = fmix_pre((uint32_t)__ldg(col + j));
+                const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - id0));
 #pragma unroll 4
-                for (uint32_t i = 0; i < b; ++i) {
+                for (uint32_t i = 0; i < bv; ++i) {
                     const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
                     atomicOr(&f[p >> 5], 1u << (p & 31u));
                 }
@@ -102,7 +117,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
 template <int kMaxWords32>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_hub(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, uint32_t l, uint32_t b,
-    uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t chunk, int32_t *hub_base) {
+    uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t chunk, int32_t *hub_base,
+    BatchMap bm) {
     __shared__ uint32_t f[kMaxWords32];
     __shared__ int2 task;
     __shared__ uint32_t pre_s[16];
@@ -124,9 +140,12 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_hub(
         const int32_t a = row_ptr[v], e = row_ptr[v + 1];
         const int32_t c0 = a + task.y * chunk;
         const int32_t c1 = min(e, c0 + chunk);
+        uint32_t bv = b;
+        int32_t id0 = 0;
+        vertex_params(bm, v, bv, id0);
         for (int32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-            const uint32_t px = fmix_pre((uint32_t)__ldg(col + j));
-            for (uint32_t i = 0; i < b; ++i) {
+            const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - id0));
+            for (uint32_t i = 0; i < bv; ++i) {
                 const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
                 atomicOr(&f[p >> 5], 1u << (p & 31u));
             }
@@ -399,22 +418,23 @@ size_t build_workspace_bytes(int64_t nnz) {
 
 cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32_t n, uint32_t l,
                                uint32_t b, uint32_t seed, uint8_t *data, int64_t stride,
-                               int32_t *hub_base, cudaStream_t s) {
+                               int32_t *hub_base, cudaStream_t s, const BatchMap *bmap) {
     if (n == 0) return cudaSuccess;
+    const BatchMap bm = bmap ? *bmap : BatchMap{};
     launch_fill_u64(reinterpret_cast<uint64_t *>(hub_base), 2, 0, s);
     const int grid = build_grid(n);
     const int hub_grid = device_info().sm_count * 4;
     if (stride <= 128) {
         k_bloom_warp<32><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
-                                                        kBloomHub, kBloomChunk, hub_base);
+                                                        kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<32><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
-                                                           kBloomChunk, hub_base);
+                                                           kBloomChunk, hub_base, bm);
         note_launch(2);
     } else {
         k_bloom_warp<256><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
-                                                         kBloomHub, kBloomChunk, hub_base);
+                                                         kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<256><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
-                                                            kBloomChunk, hub_base);
+                                                            kBloomChunk, hub_base, bm);
         note_launch(2);
     }
     return cudaGetLastError();

@@ -33,6 +33,7 @@ SYMBOLS = [
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
+    "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
 ]
 
 
@@ -57,6 +58,11 @@ class Outputs(ctypes.Structure):
     _fields_ = [("tc", ctypes.c_void_p), ("lcc", ctypes.c_void_p), ("tri", ctypes.c_void_p),
                 ("edge_cn", ctypes.c_void_p), ("edge_jac", ctypes.c_void_p), ("edge_count", ctypes.c_void_p),
                 ("edge_aux", ctypes.c_void_p), ("hist", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("bits", ctypes.c_uint32), ("b", ctypes.c_uint32), ("variant", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 TC_RESULT_BYTES = 48
@@ -101,6 +107,12 @@ def lib() -> ctypes.CDLL:
                 "pg_kernel_launches": (ctypes.c_uint64, []),
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
                 "pg_triangle_count_noalloc": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, vp]),
+                "pg_batch_autotune": (i32, [vp, vp, i32, ctypes.c_double, P(BatchConfig)]),
+                "pg_batch_workspace_bytes": (sz, [P(Csr), i32, vp, P(BatchConfig)]),
+                "pg_batch_create": (i32, [P(Csr), i32, vp, P(BatchConfig), u32, vp, sz, vp, vp, vp, vp,
+                                          P(vp)]),
+                "pg_batch_run": (i32, [vp, vp]),
+                "pg_batch_destroy": (i32, [vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -394,3 +406,82 @@ def triangle_count_noalloc(g: Graph, sk: Sketch, est: int, *, out: torch.Tensor 
     _check(lib().pg_triangle_count_noalloc(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(out), _stream()),
            "pg_triangle_count_noalloc")
     return read_tc_result(out) if read else out
+
+
+# -------------------------------------------------------------------- batch
+def batch_autotune(n, nnz, budget: float):
+    """pg_batch_autotune over host arrays of per-graph vertex and entry
+    counts: returns a list of (bits, b) per graph."""
+    import numpy as np
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    nnz = np.ascontiguousarray(nnz, dtype=np.int64)
+    G = len(n)
+    cfg = (BatchConfig * max(G, 1))()
+    _check(lib().pg_batch_autotune(n.ctypes.data_as(ctypes.c_void_p), nnz.ctypes.data_as(ctypes.c_void_p), G,
+                                   float(budget), cfg), "pg_batch_autotune")
+    return [(cfg[i].bits, cfg[i].b) for i in range(G)]
+
+
+class Batch:
+    """pg_batch_*: G graphs as one block-diagonal CSR (graph i = vertices
+    voff[i] .. voff[i+1]-1), each with its own Bloom (bits, b); one run
+    computes every graph's triangle count and every vertex's LCC. Owns its
+    workspace and outputs; `run()` enqueues on the current stream (captured
+    as a CUDA graph on first use there)."""
+
+    def __init__(self, g: Graph, voff, configs, seed: int = 1, *, want_tri: bool = False):
+        import numpy as np
+        self.g = g
+        self.voff = np.ascontiguousarray(voff, dtype=np.int32)
+        self.G = len(self.voff) - 1
+        self.cfg = (BatchConfig * self.G)()
+        for i, c in enumerate(configs):
+            bits, b = c[0], c[1]
+            variant = c[2] if len(c) > 2 else 0
+            self.cfg[i] = BatchConfig(bits, b, variant, 0)
+        self._csr = g.csr()
+        vp = self.voff.ctypes.data_as(ctypes.c_void_p)
+        nbytes = lib().pg_batch_workspace_bytes(ctypes.byref(self._csr), self.G, vp, self.cfg)
+        if nbytes == 0:
+            raise PGError(-1, "pg_batch_workspace_bytes", lib().pg_last_error().decode(errors="replace"))
+        self.ws = _dev_bytes(nbytes, g.device)
+        self.tc = torch.zeros(self.G * TC_RESULT_BYTES, dtype=torch.uint8, device=g.device)
+        self.lcc = torch.zeros(g.n, dtype=torch.float32, device=g.device)
+        self.tri = torch.zeros(g.n, dtype=torch.float64, device=g.device) if want_tri else None
+        h = ctypes.c_void_p()
+        _check(lib().pg_batch_create(ctypes.byref(self._csr), self.G, vp, self.cfg, seed, _ptr(self.ws),
+                                     self.ws.numel(), _ptr(self.tc), _ptr(self.lcc), _ptr(self.tri), _stream(),
+                                     ctypes.byref(h)), "pg_batch_create")
+        self._h = h
+
+    @property
+    def variants(self):
+        return [self.cfg[i].variant for i in range(self.G)]
+
+    def run(self, stream: int | None = None):
+        _check(lib().pg_batch_run(self._h, _stream() if stream is None else stream), "pg_batch_run")
+
+    def results(self):
+        """Per-graph dicts of the triangle-count result (synchronises)."""
+        raw = self.tc.cpu().numpy().tobytes()
+        out = []
+        for i in range(self.G):
+            edges, count_sum, exact_tc, _, est_tc, est_tc_alt = struct.unpack_from("<QQQQdd", raw, 48 * i)
+            out.append({"edges": edges, "count_sum": count_sum, "exact_tc": exact_tc, "est_tc": est_tc,
+                        "est_tc_alt": est_tc_alt})
+        return out
+
+    def est_tc(self) -> torch.Tensor:
+        """Per-graph triangle-count estimates as a device float64 view."""
+        return self.tc.view(self.G, 6 * 8).view(torch.float64)[:, 4]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -78,17 +78,18 @@ def erdos_renyi(n: int, avg_deg: float, seed: int, device="cpu"):
 
 
 def rmat(scale: int, edgefactor: int, seed: int, a=0.57, b=0.19, c=0.19, d=0.05,
-         permute: bool = True, device="cpu", n: int | None = None):
+         permute: bool = True, device="cpu", n: int | None = None, samples: int | None = None):
     """R-MAT / Kronecker generator (the paper's Kronecker graphs, Sec. VIII-A).
 
     Draws edgefactor * 2^scale directed samples; at each of `scale` levels
     one uniform number picks a quadrant with probabilities (a, b, c, d).
     With `permute`, vertex labels are relabelled by a seeded permutation.
     With `n` < 2^scale, samples touching an id >= n are rejected (used by
-    the batch mix, where n is not a power of two)."""
+    the batch mix, where n is not a power of two); `samples` overrides the
+    sample count edgefactor * 2^scale."""
     N = 1 << scale
     n_out = N if n is None else int(n)
-    samples = edgefactor * N
+    samples = edgefactor * N if samples is None else int(samples)
     gd = _rng(seed, device)
     u = torch.zeros(samples, dtype=torch.int64, device=device)
     v = torch.zeros(samples, dtype=torch.int64, device=device)
@@ -147,3 +148,50 @@ def random_pairs(n: int, count: int, seed: int, row_ptr=None, col=None, edge_fra
         out[n_edge:, 0] = torch.randint(0, n, (count - n_edge,), generator=g, device=device, dtype=torch.int32)
         out[n_edge:, 1] = torch.randint(0, n, (count - n_edge,), generator=g, device=device, dtype=torch.int32)
     return out
+
+
+def batch_mix(graphs: int, seed: int, log2_n=(8, 16), deg_median: float = 12.0, deg_sigma: float = 0.6,
+              deg_range=(4.0, 64.0), device="cpu"):
+    """A mix of small graphs of uneven sizes (the batching workload):
+    graphs alternate Erdos-Renyi / R-MAT (even index ER, odd R-MAT); each
+    has n = floor(2^U(lo, hi)) vertices and a target average degree
+    clip(lognormal(ln median, sigma), range). R-MAT graphs use scale
+    ceil(log2 n) with ids >= n rejected, drawing enough samples that about
+    n * degree / 2 land inside. Returns a list of (row_ptr, col) pairs."""
+    rs = np.random.Generator(np.random.PCG64(int(seed)))
+    ns = np.floor(2.0 ** rs.uniform(log2_n[0], log2_n[1], graphs)).astype(np.int64)
+    degs = np.clip(rs.lognormal(np.log(deg_median), deg_sigma, graphs), deg_range[0], deg_range[1])
+    out = []
+    for i in range(graphs):
+        n, dg = int(ns[i]), float(degs[i])
+        gseed = int(seed) * 1_000_003 + i
+        if i % 2 == 0:
+            out.append(erdos_renyi(n, dg, gseed, device=device))
+        else:
+            scale = max(1, int(np.ceil(np.log2(n))))
+            keep = (n / float(1 << scale)) ** 2
+            samples = int(round(n * dg / 2.0 / keep))
+            out.append(rmat(scale, 1, gseed, device=device, n=n, samples=samples))
+    return out
+
+
+def block_diagonal(parts):
+    """Concatenate graphs into one CSR with global ids: graph i's vertices
+    become voff[i] .. voff[i+1]-1. Returns (row_ptr int32, col int32, voff
+    int64 numpy [G+1])."""
+    ns = [int(rp.numel()) - 1 for rp, _ in parts]
+    voff = np.zeros(len(parts) + 1, dtype=np.int64)
+    voff[1:] = np.cumsum(ns)
+    nnz = [int(cl.numel()) for _, cl in parts]
+    eoff = np.zeros(len(parts) + 1, dtype=np.int64)
+    eoff[1:] = np.cumsum(nnz)
+    if eoff[-1] >= 2**31 or voff[-1] >= 2**31:
+        raise ValueError("batch has 2^31 or more vertices or CSR entries")
+    device = parts[0][0].device if parts else "cpu"
+    row_ptr = torch.empty(int(voff[-1]) + 1, dtype=torch.int32, device=device)
+    col = torch.empty(int(eoff[-1]), dtype=torch.int32, device=device)
+    for i, (rp, cl) in enumerate(parts):
+        row_ptr[voff[i]:voff[i + 1]] = rp[:-1] + int(eoff[i])
+        col[eoff[i]:eoff[i + 1]] = cl + int(voff[i])
+    row_ptr[-1] = int(eoff[-1])
+    return row_ptr, col, voff
