@@ -67,6 +67,7 @@ typedef int32_t pg_status;
 #define PG_ERR_NOT_FOUND     (-7) /* unknown ticket / handle */
 #define PG_ERR_BUSY          (-8) /* result not ready yet / queue full */
 #define PG_ERR_UNSUPPORTED   (-9) /* a parameter combination this build does not implement */
+#define PG_ERR_CANCELLED    (-10) /* a served request was cancelled or its server shut down */
 
 /* Human-readable name of a status code (static string). */
 const char *pg_status_string(pg_status status);
@@ -344,6 +345,116 @@ pg_status pg_batch_run(pg_batch *batch, pg_stream_t stream);
 /* Free the host state and the captured graph (not the workspace). NULL is a
  * no-op. */
 pg_status pg_batch_destroy(pg_batch *batch);
+
+/* -------------------------------------------------------------- serving --
+ * A request loop over one resident graph and its sketches: vertex-pair
+ * similarity queries (the common-neighbour and Jaccard estimates of Sec. III
+ * and IV, as in link prediction) and triangle counts of induced subgraphs
+ * (Sec. VII on G[S]), with continuous batching.
+ *
+ * A host scheduler thread owned by the server admits queued requests in
+ * arrival order while the arena (caller-owned DEVICE memory) has room for
+ * them, and keeps the GPU busy with the admitted ones:
+ *   - pair requests are cut into tiles of 1024 pairs; every launch of the
+ *     pair kernel takes tiles round-robin from all admitted pair requests
+ *     (up to iteration_pairs pairs), so a request that arrives while others
+ *     run joins the next launch and small requests finish without waiting
+ *     for large ones;
+ *   - each subgraph request runs its own pipeline (membership marks,
+ *     induced degrees, scan, induced CSR with local ids; then edge index,
+ *     Bloom sketches of the induced neighbourhoods and the fused pass, or the
+ *     exact count) on one of `streams` streams, overlapping with the pair
+ *     launches and with each other.
+ * Results are deterministic: a request's answer does not depend on what else
+ * is in flight (the pair kernel computes each pair alone; a subgraph's
+ * vertices are sorted and deduplicated, and its sketches hash their local
+ * ids in that order).
+ * No kernel waits on the host: the scheduler polls CUDA events, and pg_poll
+ * waits on the host with the caller's time limit. */
+#define PG_REQ_PAIRS       1
+#define PG_REQ_SUBGRAPH_TC 2
+
+typedef struct pg_server_opts {
+    int32_t streams;         /* concurrent subgraph pipelines (0: 4) */
+    int32_t max_inflight;    /* admitted requests at once (0: 1024) */
+    int64_t iteration_pairs; /* pairs per pair-kernel launch at most (0: 262144) */
+    size_t pinned_bytes;     /* page-locked host staging the server allocates (0: 256 MiB) */
+    uint32_t sub_bits;       /* Bloom filter of subgraph requests (0: 512 bits) */
+    uint32_t sub_b;          /* its hash count (0: 2) */
+    uint32_t sub_seed;       /* its seed (0: 1) */
+    int32_t reserved;
+} pg_server_opts;
+
+typedef struct pg_request {
+    int32_t kind;      /* PG_REQ_PAIRS or PG_REQ_SUBGRAPH_TC */
+    int32_t estimator; /* pairs: PG_EST_BF_AND, PG_EST_BF_L (the server's Bloom sketch), PG_EST_KH (its
+                          k-Hash sketch) or PG_EST_EXACT (merge of the two rows);
+                          subgraph: PG_EST_BF_AND, PG_EST_BF_L or PG_EST_EXACT */
+    int64_t count;     /* pairs P, or vertices |S| (duplicates allowed) */
+    const int32_t *data; /* HOST: pairs int32 [2P] (u, v), or vertex ids [|S|]; read when the request is
+                            admitted, so it must stay valid until pg_poll returns its response */
+    float *cn;         /* HOST float [P] or NULL: common-neighbour estimate per pair */
+    float *jac;        /* HOST float [P] or NULL: Jaccard estimate per pair */
+} pg_request;
+
+typedef struct pg_response {
+    int32_t status;   /* PG_OK, PG_ERR_CANCELLED, or the error that ended the request */
+    int32_t kind;
+    int64_t count;    /* pairs answered, or |S| after deduplication */
+    pg_tc_result tc;  /* subgraph: as pg_triangle_count on G[S] (tc.edges = edges of G[S]) */
+    double queue_us;  /* submit -> admission */
+    double total_us;  /* submit -> result on the host */
+} pg_response;
+
+typedef struct pg_server pg_server;
+
+/* Arena bytes a server reserves for itself (estimator tables, pair tile
+ * descriptors, one membership bitmap of n bits per stream); requests use the
+ * rest. opts may be NULL (defaults). */
+size_t pg_server_reserved_bytes(const pg_csr *g, const pg_server_opts *opts);
+
+/* Create a server over the DEVICE CSR g and n_sketches resident sketches (at
+ * most one Bloom of <= 8192 bits and one k-Hash of k <= 1024; pair requests for an estimator whose sketch
+ * is absent fail with PG_ERR_UNSUPPORTED). The CSR, the sketches and the
+ * arena stay owned by the caller and must outlive the server; the server
+ * copies the row offsets to the host once (admission bounds). Starts the
+ * scheduler thread on the current device. Errors: PG_ERR_INVALID_ARG,
+ * PG_ERR_NO_MEMORY (arena below pg_server_reserved_bytes), PG_ERR_CUDA. */
+pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, int32_t n_sketches,
+                           void *arena, size_t arena_bytes, const pg_server_opts *opts, pg_server **out);
+
+/* Queue a request; *ticket identifies it for pg_poll / pg_cancel. Checks the
+ * arguments (vertex ids must lie in [0, n); pair ids outside give 0 answers)
+ * and that the request can ever fit the arena and the staging memory
+ * (PG_ERR_NO_MEMORY otherwise); never waits for the GPU. */
+pg_status pg_submit(pg_server *server, const pg_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0: do not wait) for the request to
+ * complete. PG_OK: *out holds the response, the outputs are written, and the
+ * ticket is released. PG_ERR_BUSY: not complete yet. PG_ERR_NOT_FOUND:
+ * unknown or already collected ticket. */
+pg_status pg_poll(pg_server *server, uint64_t ticket, pg_response *out, int64_t timeout_us);
+
+/* Cancel a request that has not been admitted yet (its response then has
+ * status PG_ERR_CANCELLED). PG_ERR_BUSY if it already runs (it completes
+ * normally), PG_ERR_NOT_FOUND for an unknown ticket. */
+pg_status pg_cancel(pg_server *server, uint64_t ticket);
+
+/* Counters since creation. */
+typedef struct pg_server_stats {
+    uint64_t submitted, completed, cancelled, failed;
+    uint64_t pair_launches;  /* launches of the pair kernel */
+    uint64_t pairs;          /* pairs answered */
+    uint64_t subgraphs;      /* subgraph pipelines run */
+    uint64_t queued, running;
+    uint64_t arena_used, arena_peak, arena_bytes;
+} pg_server_stats;
+pg_status pg_server_stats_get(pg_server *server, pg_server_stats *out);
+
+/* Stop the server: requests not yet admitted are cancelled, admitted ones
+ * run to completion on the GPU (their responses are discarded), then the
+ * thread, streams and staging memory are released. NULL is a no-op. */
+pg_status pg_server_destroy(pg_server *server);
 
 #ifdef __cplusplus
 }

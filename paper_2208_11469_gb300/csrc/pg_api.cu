@@ -184,6 +184,7 @@ const char *pg_status_string(pg_status s) {
         case PG_ERR_NOT_FOUND: return "PG_ERR_NOT_FOUND";
         case PG_ERR_BUSY: return "PG_ERR_BUSY";
         case PG_ERR_UNSUPPORTED: return "PG_ERR_UNSUPPORTED";
+        case PG_ERR_CANCELLED: return "PG_ERR_CANCELLED";
         default: return "PG_ERR_UNKNOWN";
     }
 }

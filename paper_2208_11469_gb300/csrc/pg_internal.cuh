@@ -147,6 +147,11 @@ cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_
                               const int64_t *hoff, int32_t v_lo, int32_t v_hi, uint64_t *hist, double *S,
                               double *table_ws, cudaStream_t s);
 int32_t batch_variants(uint32_t bits, int32_t *out);
+// The estimator table of (kind, estimator, l, b, k) into table_ws
+// (intersect_table_bytes): double [len] | uint64 fixed point [len] | float [len],
+// indexed by the integer count (k-Hash: c / (k + c), scaled by d_u + d_v by the user).
+cudaError_t launch_estimator_table(double *table_ws, int32_t kind, int32_t estimator, uint32_t l, uint32_t b,
+                                   uint32_t k, cudaStream_t s);
 cudaError_t launch_batch_finalize(const uint64_t *hist, const int64_t *hoff, const uint32_t *bits_of,
                                   const uint8_t *b_of, int32_t graphs, int32_t estimator, pg_tc_result *out,
                                   cudaStream_t s);

@@ -1047,6 +1047,13 @@ cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_
     }
 }
 
+cudaError_t launch_estimator_table(double *table_ws, int32_t kind, int32_t estimator, uint32_t l, uint32_t b,
+                                   uint32_t k, cudaStream_t s) {
+    k_table<<<1, 256, 0, s>>>(table_ws, (int32_t)table_len(kind, l, k), kind, estimator, l, b, k);
+    note_launch();
+    return cudaGetLastError();
+}
+
 int32_t batch_variants(uint32_t bits, int32_t *out) {
     switch (bits) {
         case 64: out[0] = 1; out[1] = 2; return 2;

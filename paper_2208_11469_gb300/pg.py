@@ -21,7 +21,7 @@ from . import build as _build
 OK = 0
 ERR = {0: "PG_OK", -1: "PG_ERR_INVALID_ARG", -2: "PG_ERR_INVALID_GRAPH", -3: "PG_ERR_TOO_LARGE",
        -4: "PG_ERR_NO_MEMORY", -5: "PG_ERR_CUDA", -6: "PG_ERR_TIMEOUT", -7: "PG_ERR_NOT_FOUND",
-       -8: "PG_ERR_BUSY", -9: "PG_ERR_UNSUPPORTED"}
+       -8: "PG_ERR_BUSY", -9: "PG_ERR_UNSUPPORTED", -10: "PG_ERR_CANCELLED"}
 SK_BLOOM, SK_KHASH, SK_1HASH = 1, 2, 3
 EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
 CSR_CODES = {0: "ok", 1: "bad_row_ptr", 2: "out_of_range", 3: "unsorted", 4: "self_loop", 5: "asymmetric"}
@@ -34,7 +34,10 @@ SYMBOLS = [
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
+    "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_poll", "pg_cancel", "pg_server_stats_get",
+    "pg_server_destroy",
 ]
+REQ_PAIRS, REQ_SUBGRAPH_TC = 1, 2
 
 
 class PGError(RuntimeError):
@@ -63,6 +66,33 @@ class Outputs(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("bits", ctypes.c_uint32), ("b", ctypes.c_uint32), ("variant", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("iteration_pairs", ctypes.c_int64),
+                ("pinned_bytes", ctypes.c_size_t), ("sub_bits", ctypes.c_uint32), ("sub_b", ctypes.c_uint32),
+                ("sub_seed", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("estimator", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("data", ctypes.c_void_p), ("cn", ctypes.c_void_p), ("jac", ctypes.c_void_p)]
+
+
+class TcResult(ctypes.Structure):
+    _fields_ = [("edges", ctypes.c_uint64), ("count_sum", ctypes.c_uint64), ("exact_tc", ctypes.c_uint64),
+                ("reserved", ctypes.c_uint64), ("est_tc", ctypes.c_double), ("est_tc_alt", ctypes.c_double)]
+
+
+class Response(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("count", ctypes.c_int64),
+                ("tc", TcResult), ("queue_us", ctypes.c_double), ("total_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_uint64) for nm in
+                ("submitted", "completed", "cancelled", "failed", "pair_launches", "pairs", "subgraphs", "queued",
+                 "running", "arena_used", "arena_peak", "arena_bytes")]
 
 
 TC_RESULT_BYTES = 48
@@ -113,6 +143,13 @@ def lib() -> ctypes.CDLL:
                                           P(vp)]),
                 "pg_batch_run": (i32, [vp, vp]),
                 "pg_batch_destroy": (i32, [vp]),
+                "pg_server_reserved_bytes": (sz, [P(Csr), P(ServerOpts)]),
+                "pg_server_create": (i32, [P(Csr), P(P(SketchDesc)), i32, vp, sz, P(ServerOpts), P(vp)]),
+                "pg_submit": (i32, [vp, P(Request), P(ctypes.c_uint64)]),
+                "pg_poll": (i32, [vp, ctypes.c_uint64, P(Response), i64]),
+                "pg_cancel": (i32, [vp, ctypes.c_uint64]),
+                "pg_server_stats_get": (i32, [vp, P(ServerStats)]),
+                "pg_server_destroy": (i32, [vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -479,6 +516,102 @@ class Batch:
         if getattr(self, "_h", None):
             lib().pg_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """pg_server_*: a request loop over the resident graph `g` and its
+    sketches (see include/pg.h). Requests take and return host numpy arrays;
+    the arena is a device tensor owned here."""
+
+    def __init__(self, g: Graph, sketches, arena_bytes: int, *, streams: int = 0, max_inflight: int = 0,
+                 iteration_pairs: int = 0, pinned_bytes: int = 0, sub_bits: int = 0, sub_b: int = 0,
+                 sub_seed: int = 0):
+        self.g = g
+        self._descs = [sk.desc() for sk in sketches]
+        self._sketches = list(sketches)
+        arr = (ctypes.POINTER(SketchDesc) * max(len(self._descs), 1))(*[ctypes.pointer(d) for d in self._descs])
+        self._arr = arr
+        self.opts = ServerOpts(streams, max_inflight, iteration_pairs, pinned_bytes, sub_bits, sub_b, sub_seed, 0)
+        self._csr = g.csr()
+        self.arena = _dev_bytes(arena_bytes, g.device)
+        h = ctypes.c_void_p()
+        torch.cuda.synchronize()
+        _check(lib().pg_server_create(ctypes.byref(self._csr), arr, len(self._descs), _ptr(self.arena),
+                                      self.arena.numel(), ctypes.byref(self.opts), ctypes.byref(h)),
+               "pg_server_create")
+        self._h = h
+        self._live = {}  # ticket -> arrays kept alive until the response is collected
+
+    @staticmethod
+    def reserved_bytes(g: Graph, **opts) -> int:
+        o = ServerOpts(opts.get("streams", 0), opts.get("max_inflight", 0), opts.get("iteration_pairs", 0),
+                       opts.get("pinned_bytes", 0), opts.get("sub_bits", 0), opts.get("sub_b", 0),
+                       opts.get("sub_seed", 0), 0)
+        c = g.csr()
+        return int(lib().pg_server_reserved_bytes(ctypes.byref(c), ctypes.byref(o)))
+
+    def submit_pairs(self, pairs, est: int, want_cn: bool = True, want_jac: bool = True) -> int:
+        import numpy as np
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        P = pairs.shape[0]
+        cn = np.empty(P, np.float32) if want_cn else None
+        jac = np.empty(P, np.float32) if want_jac else None
+        req = Request(REQ_PAIRS, est, P, pairs.ctypes.data if P else None,
+                      cn.ctypes.data if cn is not None and P else None,
+                      jac.ctypes.data if jac is not None and P else None)
+        t = ctypes.c_uint64()
+        _check(lib().pg_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "pg_submit")
+        self._live[t.value] = (pairs, cn, jac)
+        return t.value
+
+    def submit_subgraph(self, vertices, est: int) -> int:
+        import numpy as np
+        v = np.ascontiguousarray(vertices, dtype=np.int32).reshape(-1)
+        req = Request(REQ_SUBGRAPH_TC, est, v.size, v.ctypes.data if v.size else None, None, None)
+        t = ctypes.c_uint64()
+        _check(lib().pg_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "pg_submit")
+        self._live[t.value] = (v, None, None)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """The response as a dict (with 'cn'/'jac' arrays for pairs), or None
+        while the request runs. Raises PGError for unknown tickets."""
+        r = Response()
+        st = lib().pg_poll(self._h, ticket, ctypes.byref(r), int(timeout_us))
+        if st == -8:
+            return None
+        _check(st, "pg_poll")
+        _, cn, jac = self._live.pop(ticket, (None, None, None))
+        tc = {nm: getattr(r.tc, nm) for nm, _ in TcResult._fields_ if nm != "reserved"}
+        return {"status": r.status, "kind": r.kind, "count": r.count, "tc": tc, "queue_us": r.queue_us,
+                "total_us": r.total_us, "cn": cn, "jac": jac}
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        r = self.poll(ticket, int(timeout_s * 1e6))
+        if r is None:
+            raise PGError(-6, "Server.wait", f"ticket {ticket} not complete after {timeout_s} s")
+        return r
+
+    def cancel(self, ticket: int) -> int:
+        return int(lib().pg_cancel(self._h, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().pg_server_stats_get(self._h, ctypes.byref(s)), "pg_server_stats_get")
+        return {nm: getattr(s, nm) for nm, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _check(lib().pg_server_destroy(self._h), "pg_server_destroy")
+            self._h = None
+            self._live.clear()
 
     def __del__(self):
         try:

@@ -195,3 +195,55 @@ def block_diagonal(parts):
         col[eoff[i]:eoff[i + 1]] = cl + int(voff[i])
     row_ptr[-1] = int(eoff[-1])
     return row_ptr, col, voff
+
+
+def bfs_ball(row_ptr, col, start: int, target_edges: int):
+    """Vertices of a breadth-first ball around `start`: whole BFS levels
+    while the induced subgraph has fewer than target_edges undirected edges,
+    then the shortest prefix of the next level (in BFS discovery order) that
+    reaches the target (or the whole component). Host numpy; returns int32
+    vertex ids in BFS order (the serving workload's induced-subgraph
+    queries)."""
+    rp = np.asarray(row_ptr.cpu() if hasattr(row_ptr, "cpu") else row_ptr, dtype=np.int64)
+    cl = np.asarray(col.cpu() if hasattr(col, "cpu") else col, dtype=np.int64)
+    n = rp.size - 1
+    inside = np.zeros(n, dtype=bool)
+
+    def rows(vs):
+        lens = rp[vs + 1] - rp[vs]
+        idx = np.repeat(rp[vs] - np.cumsum(np.concatenate([[0], lens[:-1]])), lens) + np.arange(int(lens.sum()))
+        return cl[idx], np.repeat(np.arange(vs.size), lens)
+
+    def induced_edges(vs):
+        mark = np.zeros(n, dtype=bool)
+        mark[vs] = True
+        nb, _ = rows(vs)
+        return int(mark[nb].sum()) // 2
+
+    ball = np.asarray([start], dtype=np.int64)
+    inside[start] = True
+    frontier = ball
+    while frontier.size:
+        nb, _ = rows(frontier)
+        # next level in discovery order: first occurrence of each new vertex
+        new = nb[~inside[nb]]
+        _, first = np.unique(new, return_index=True)
+        level = new[np.sort(first)]
+        if level.size == 0:
+            break
+        cand = np.concatenate([ball, level])
+        if induced_edges(cand) < target_edges:
+            inside[level] = True
+            ball = cand
+            frontier = level
+            continue
+        lo, hi = 1, level.size  # shortest prefix reaching the target
+        while lo < hi:
+            mid = (lo + hi) // 2
+            if induced_edges(np.concatenate([ball, level[:mid]])) >= target_edges:
+                hi = mid
+            else:
+                lo = mid + 1
+        ball = np.concatenate([ball, level[:lo]])
+        break
+    return ball.astype(np.int32)
