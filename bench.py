@@ -1,7 +1,7 @@
 """Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096]
+                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096|serve22]
                     [--impl ours|reference]
 
 A step is one pass of the whole sketched path over the synthetic graph of the
@@ -53,6 +53,11 @@ WORKLOADS = {
     # lognormal (median 12, clipped to 4..64); per-graph Bloom length and hash count from the
     # autotuner at 25% of each graph's CSR bytes; one captured batch run against one launch per graph
     "batch4096": dict(batch=4096, budget=0.25, seed=1),
+    # serving: resident R-MAT scale 22, edge factor 16, Bloom 512 bits b = 2 and k-Hash k = 32 on the
+    # device; pair requests of lognormal size (median 256, sigma 2, clipped to 1..65536), half existing
+    # edges and half random pairs, and induced-subgraph triangle counts of BFS balls of 10^U(3,6) edges
+    "serve22": dict(serve=True, gen=("rmat", 22, 16, 22), bits=512, b=2, khash=32, pair_requests=2000,
+                    subgraph_requests=12, subgraph_share=0.02),
 }
 
 
@@ -86,6 +91,9 @@ def generate(workload: str, device):
     from paper_2208_11469_gb300 import synth
     if "batch" in WORKLOADS[workload]:
         return generate_batch(workload, device)
+    if "serve" in WORKLOADS[workload]:
+        kind, scale, ef, seed = WORKLOADS[workload]["gen"]
+        return synth.rmat(scale, ef, seed=seed, device=device)
     kind, *a = WORKLOADS[workload]["gen"]
     if kind == "rmat":
         scale, ef, seed = a
@@ -608,6 +616,245 @@ def run_batch(args, ws, rank, dev):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- serving
+def serve_requests(workload, rp, cl, seed=7):
+    """The request set: pair requests (sizes lognormal, half edges and half
+    random pairs) and induced-subgraph requests (BFS balls of 10^U(3,6)
+    edges), interleaved at random. Host numpy arrays."""
+    from paper_2208_11469_gb300 import synth
+    w = WORKLOADS[workload]
+    rng = np.random.default_rng(seed)
+    n = rp.numel() - 1
+    sizes = np.clip(np.round(rng.lognormal(np.log(256.0), 2.0, w["pair_requests"])), 1, 65536).astype(np.int64)
+    allp = synth.random_pairs(n, int(sizes.sum()), seed, rp, cl, device=rp.device).cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    reqs = [("pairs", allp[offs[i]:offs[i + 1]]) for i in range(sizes.size)]
+    rp_h, cl_h = rp.cpu().numpy(), cl.cpu().numpy()
+    for i in range(w["subgraph_requests"]):
+        j = int(rng.integers(0, cl_h.size))
+        v = int(np.searchsorted(rp_h, j, side="right") - 1)
+        reqs.append(("sub", synth.bfs_ball(rp_h, cl_h, v, int(10 ** rng.uniform(3, 6)))))
+    order = rng.permutation(len(reqs))
+    return [reqs[i] for i in order], rp_h, cl_h
+
+
+def induced_edges(rp_h, cl_h, S):
+    mark = np.zeros(rp_h.size - 1, dtype=bool)
+    mark[S] = True
+    lens = rp_h[S + 1] - rp_h[S]
+    idx = np.repeat(rp_h[S] - np.cumsum(np.concatenate([[0], lens[:-1]])), lens) + np.arange(int(lens.sum()))
+    return int(mark[cl_h[idx]].sum()) // 2
+
+
+def serve_burst(sv, reqs, est_pairs, est_sub, pg, pinned=None):
+    """Submit every request at once and collect them all: the pair requests
+    as one concatenated page-locked array (pg_submit_many, used in place by
+    the GPU), the subgraph requests in a second pg_submit_many. Returns
+    (seconds, responses in request order, pair outputs in request order)."""
+    if pinned is None:
+        pinned = serve_pinned(reqs, pg)
+    pidx, sidx, offs, buf = pinned
+    t0 = time.perf_counter()
+    tp, cn, jac = sv.submit_pairs_many(buf, offs, est_pairs, pinned=True)
+    ts, _ = sv.submit_many([("sub", reqs[i][1], est_sub) for i in sidx])
+    rp_ = sv.poll_many(tp, timeout_us=600_000_000)
+    rs_ = sv.poll_many(ts, timeout_us=600_000_000)
+    dt = time.perf_counter() - t0
+    resp = np.zeros(len(reqs), dtype=rp_.dtype)
+    outs = [None] * len(reqs)
+    resp[pidx] = rp_
+    resp[sidx] = rs_
+    for k, i in enumerate(pidx):
+        outs[i] = (cn[offs[k]:offs[k + 1]], jac[offs[k]:offs[k + 1]])
+    return dt, resp, outs
+
+
+def serve_pinned(reqs, pg):
+    """The pair requests of a request set concatenated in page-locked memory."""
+    pidx = [i for i, (k, _) in enumerate(reqs) if k == "pairs"]
+    sidx = [i for i, (k, _) in enumerate(reqs) if k != "pairs"]
+    sizes = [reqs[i][1].shape[0] for i in pidx]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    buf = pg.pinned_empty((int(offs[-1]), 2), np.int32)
+    if pidx:
+        buf[...] = np.concatenate([reqs[i][1] for i in pidx])
+    return pidx, sidx, offs, buf
+
+
+def serve_poisson(sv, reqs, rate, duration, est_pairs, est_sub, seed=3):
+    """Open-loop Poisson arrivals at `rate` requests/s for `duration` s,
+    cycling through the request set; a second thread collects. Returns the
+    responses with their kinds."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, int(rate * duration) + 1)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < duration]
+    tickets = []
+    lock = threading.Lock()
+    done = []
+
+    def collect():
+        i = 0
+        while True:
+            with lock:
+                if i >= len(tickets):
+                    if finished[0]:
+                        break
+                    t = None
+                else:
+                    t = tickets[i]
+            if t is None:
+                time.sleep(0.0005)
+                continue
+            kind, tk = t
+            done.append((kind, sv.wait(tk, 600.0)))
+            i += 1
+
+    finished = [False]
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for i, at in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        kind, x = reqs[i % len(reqs)]
+        tk = sv.submit_pairs(x, est_pairs) if kind == "pairs" else sv.submit_subgraph(x, est_sub)
+        with lock:
+            tickets.append((kind, tk))
+    with lock:
+        finished[0] = True
+    th.join()
+    return done, time.perf_counter() - t0
+
+
+def run_serve(args, ws, rank, dev):
+    from paper_2208_11469_gb300 import pg
+    w = WORKLOADS[args.workload]
+    rp, cl = generate(args.workload, dev)
+    g = pg.graph(rp, cl, build_index=True)
+    bf = pg.build_bloom(g, w["bits"], w["b"], seed=1)
+    kh = pg.build_minhash(g, pg.SK_KHASH, w["khash"], seed=1)
+    reqs, rp_h, cl_h = serve_requests(args.workload, rp, cl)
+    pairs_total = sum(x.shape[0] for k, x in reqs if k == "pairs")
+    sub_edges = {id(x): induced_edges(rp_h, cl_h, x) for k, x in reqs if k == "sub"}
+    units = pairs_total + sum(sub_edges.values())
+    torch.cuda.synchronize()
+    sv = pg.Server(g, [bf, kh], 6 << 30)
+    pinned = serve_pinned(reqs, pg)
+    for _ in range(args.warmup):
+        serve_burst(sv, reqs, pg.EST_BF_AND, pg.EST_BF_AND, pg, pinned)
+    st0 = sv.stats()
+    times = []
+    with ClockSampler(dev.index or 0) as clk:
+        for _ in range(args.steps):
+            dt, out, _ = serve_burst(sv, reqs, pg.EST_BF_AND, pg.EST_BF_AND, pg, pinned)
+            assert (out["status"] == 0).all()
+            times.append(dt)
+    st1 = sv.stats()
+    burst_s = float(np.median(times))
+    value = units * ws / burst_s
+    kernel_ns = st1["pair_kernel_ns"] - st0["pair_kernel_ns"]
+    pairs_timed = st1["pairs"] - st0["pairs"]
+    # k_serve_pairs roofline: per pair two 64-byte rows, the pair (8 B), four row offsets (16 B), two outputs
+    per_pair = 2 * w["bits"] / 8 + 8 + 16 + 8
+    alg = pairs_timed * per_pair
+    peak, peak_kind = peaks()
+    achieved = alg / (kernel_ns * 1e-9) / 1e9 if kernel_ns else None
+
+    # latency under open-loop Poisson arrivals, one request per pg_submit: at 70% of the burst request
+    # rate, capped at what one Python submitting thread sustains
+    rate = min(0.7 * len(reqs) / burst_s, 15000.0)
+    lat, wall = serve_poisson(sv, reqs, rate, 3.0, pg.EST_BF_AND, pg.EST_BF_AND)
+    pl = np.array([r["total_us"] for k, r in lat if k == "pairs"])
+    sl = np.array([r["total_us"] for k, r in lat if k == "sub"])
+    latency = {"offered_requests_per_s": rate, "achieved_requests_per_s": len(lat) / wall,
+               "requests": len(lat), "seconds": wall,
+               "pairs_p50_us": float(np.percentile(pl, 50)) if pl.size else None,
+               "pairs_p99_us": float(np.percentile(pl, 99)) if pl.size else None,
+               "subgraph_p50_us": float(np.percentile(sl, 50)) if sl.size else None,
+               "subgraph_p99_us": float(np.percentile(sl, 99)) if sl.size else None}
+
+    # the same requests through the server with the exact intersection
+    ex_dt, ex_out, ex_pairs = serve_burst(sv, reqs, pg.EST_EXACT, pg.EST_EXACT, pg, pinned)
+    _, est_out, est_pairs = serve_burst(sv, reqs, pg.EST_BF_AND, pg.EST_BF_AND, pg, pinned)
+    _, kh_out, kh_pairs = serve_burst(sv, reqs, pg.EST_KH, pg.EST_BF_AND, pg, pinned)
+    # accuracy on a seeded 1% sample of the requests (exact answers from the exact GPU path)
+    rng = np.random.default_rng(1)
+    sample = rng.choice(len(reqs), max(1, len(reqs) // 100), replace=False)
+    cn_err, cn_err_kh, tc_rel = [], [], []
+    for i in sample:
+        if reqs[i][0] == "pairs":
+            cn_err.append(float(np.mean(np.abs(est_pairs[i][0] - ex_pairs[i][0]))))
+            cn_err_kh.append(float(np.mean(np.abs(kh_pairs[i][0] - ex_pairs[i][0]))))
+        elif ex_out[i]["exact_tc"]:
+            tc_rel.append(abs(est_out[i]["est_tc"] - ex_out[i]["exact_tc"]) / ex_out[i]["exact_tc"])
+    sub_idx = [i for i in range(len(reqs)) if reqs[i][0] == "sub" and ex_out[i]["exact_tc"]]
+    tc_rel_all = [float(abs(est_out[i]["est_tc"] - ex_out[i]["exact_tc"]) / ex_out[i]["exact_tc"]) for i in sub_idx]
+    exact_mean_cn = float(np.mean([np.mean(ex_pairs[i][0]) for i in sample if reqs[i][0] == "pairs"]))
+    sv.close()
+
+    # one request per launch: each pair request alone through pg_jaccard_pairs (same pass kernels)
+    per = []
+    pin = {}
+    t0 = time.perf_counter()
+    n_single = 0
+    for kind, x in reqs:
+        if kind != "pairs":
+            continue
+        ts = time.perf_counter()
+        h = torch.from_numpy(x)
+        d = h.to(dev, non_blocking=False)
+        cn, jac = pg.jaccard_pairs(g, bf, pg.EST_BF_AND, d)
+        cn_h, jac_h = cn.cpu(), jac.cpu()
+        per.append((time.perf_counter() - ts) * 1e6)
+        n_single += 1
+    single_s = time.perf_counter() - t0
+    per = np.array(per)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, e, desc = oracle_sample(rp, cl, dict(w, onehash=None), w["bits"], target_s=15.0)
+        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC + " (served)", "value": value, "unit": "intersections/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": burst_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded on-device generator)",
+            "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "m": g.m, "bloom_bits": w["bits"],
+                       "bloom_b": w["b"], "khash_k": w["khash"], "requests": len(reqs),
+                       "pair_requests": w["pair_requests"], "pairs": pairs_total,
+                       "subgraph_requests": w["subgraph_requests"], "subgraph_edges": int(sum(sub_edges.values())),
+                       "step": "one burst of the whole request set, host submit to host result",
+                       "l2": "sketch tables 268 MB + 537 MB > 129 MB L2, no flush",
+                       "timing": "host wall clock (requests cross the host boundary); kernel time from CUDA events",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "k_serve_pairs", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                         "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "e2e": {"value": value, "unit": "intersections/s",
+                    "h2d_bytes_per_step": int(8 * pairs_total + 4 * sum(x.size for k, x in reqs if k == "sub")),
+                    "d2h_bytes_per_step": int(8 * pairs_total + 48 * w["subgraph_requests"]),
+                    "note": "pair inputs and outputs are page-locked host buffers the kernel reads and writes in place"},
+            "gpu_launches": int(st1["pair_launches"] - st0["pair_launches"]),
+            "latency": latency,
+            "clocks": clk.summary(),
+            "pairs_per_s": pairs_total / burst_s,
+            "exact_gpu_served": {"seconds": ex_dt, "intersections_per_s": units / ex_dt},
+            "one_request_per_launch": {"pair_requests": n_single, "seconds": single_s,
+                                       "pairs_per_s": pairs_total / single_s,
+                                       "p50_us": float(np.percentile(per, 50)), "p99_us": float(np.percentile(per, 99))},
+            "accuracy_sample": {"requests": int(sample.size), "exact_mean_cn": exact_mean_cn,
+                                "pairs_mean_abs_cn_error_bf_and": float(np.mean(cn_err)) if cn_err else None,
+                                "pairs_mean_abs_cn_error_khash": float(np.mean(cn_err_kh)) if cn_err_kh else None,
+                                "subgraph_tc_rel_error": tc_rel, "subgraph_tc_rel_error_all": tc_rel_all},
+            "server": {k: st1[k] for k in ("pair_launches", "pairs", "subgraphs", "arena_peak", "arena_bytes")},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -685,8 +932,8 @@ def main():
     from paper_2208_11469_gb300 import pg
 
     dev = torch.device("cuda", local)
-    if "batch" in WORKLOADS[args.workload]:
-        run_batch(args, ws, rank, dev)
+    if "batch" in WORKLOADS[args.workload] or "serve" in WORKLOADS[args.workload]:
+        (run_batch if "batch" in WORKLOADS[args.workload] else run_serve)(args, ws, rank, dev)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return

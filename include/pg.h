@@ -376,7 +376,7 @@ pg_status pg_batch_destroy(pg_batch *batch);
 
 typedef struct pg_server_opts {
     int32_t streams;         /* concurrent subgraph pipelines (0: 4) */
-    int32_t max_inflight;    /* admitted requests at once (0: 1024) */
+    int32_t max_inflight;    /* admitted requests at once (0: 4096) */
     int64_t iteration_pairs; /* pairs per pair-kernel launch at most (0: 262144) */
     size_t pinned_bytes;     /* page-locked host staging the server allocates (0: 256 MiB) */
     uint32_t sub_bits;       /* Bloom filter of subgraph requests (0: 512 bits) */
@@ -394,7 +394,10 @@ typedef struct pg_request {
     const int32_t *data; /* HOST: pairs int32 [2P] (u, v), or vertex ids [|S|]; read when the request is
                             admitted, so it must stay valid until pg_poll returns its response */
     float *cn;         /* HOST float [P] or NULL: common-neighbour estimate per pair */
-    float *jac;        /* HOST float [P] or NULL: Jaccard estimate per pair */
+    float *jac;        /* HOST float [P] or NULL: Jaccard estimate per pair.
+                          When data and the outputs of a pair request are all page-locked (cudaHostAlloc /
+                          cudaHostRegister), the kernels read and write them in place over the CPU-GPU link,
+                          with no staging copy and no arena bytes. */
 } pg_request;
 
 typedef struct pg_response {
@@ -429,6 +432,19 @@ pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, in
  * (PG_ERR_NO_MEMORY otherwise); never waits for the GPU. */
 pg_status pg_submit(pg_server *server, const pg_request *req, uint64_t *ticket);
 
+/* pg_submit for count requests in one call (one lock, one wake-up of the
+ * scheduler): tickets[i] for reqs[i]. All or nothing: if any request is
+ * invalid or can never fit, none is queued and the error names its index. */
+pg_status pg_submit_many(pg_server *server, const pg_request *reqs, int64_t count, uint64_t *tickets);
+
+/* pg_poll for count tickets: waits up to timeout_us until all complete.
+ * out[i] receives each completed response (whose ticket is then released),
+ * status PG_ERR_BUSY for one still running and PG_ERR_NOT_FOUND for an
+ * unknown ticket. *n_done (may be NULL) = responses with a final status.
+ * Returns PG_OK when all are final, else PG_ERR_BUSY. */
+pg_status pg_poll_many(pg_server *server, const uint64_t *tickets, int64_t count, pg_response *out,
+                       int64_t timeout_us, int64_t *n_done);
+
 /* Wait up to timeout_us microseconds (0: do not wait) for the request to
  * complete. PG_OK: *out holds the response, the outputs are written, and the
  * ticket is released. PG_ERR_BUSY: not complete yet. PG_ERR_NOT_FOUND:
@@ -448,6 +464,7 @@ typedef struct pg_server_stats {
     uint64_t subgraphs;      /* subgraph pipelines run */
     uint64_t queued, running;
     uint64_t arena_used, arena_peak, arena_bytes;
+    uint64_t pair_kernel_ns;  /* device time of the pair-kernel launches (CUDA events around each) */
 } pg_server_stats;
 pg_status pg_server_stats_get(pg_server *server, pg_server_stats *out);
 

@@ -138,59 +138,90 @@ __device__ __forceinline__ bool member(const uint32_t *__restrict__ bitmap, int3
     return (__ldg(bitmap + ((uint32_t)w >> 5)) >> ((uint32_t)w & 31u)) & 1u;
 }
 
-// Induced degree of S[i]: neighbours of S[i] that lie in S (warp per vertex).
-__global__ void __launch_bounds__(256) k_sub_degree(const int32_t *__restrict__ row_ptr,
-                                                    const int32_t *__restrict__ col,
-                                                    const int32_t *__restrict__ S, int32_t ns,
-                                                    const uint32_t *__restrict__ bitmap, int32_t *deg) {
+// Phase 1 works on chunks of at most kChunk row entries, (row i of S, first
+// entry) pairs listed by the host in row order with at least one chunk per
+// row, so a hub row is split over many warps instead of walked by one.
+constexpr int32_t kChunk = 1024;
+constexpr int kChunkUnroll = 4;  // 32-entry steps whose loads are issued together
+
+// Members of S among the chunk's entries, per chunk (warp per chunk).
+__global__ void __launch_bounds__(256) k_chunk_count(const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col,
+                                                     const int32_t *__restrict__ S,
+                                                     const int2 *__restrict__ chunks, int32_t C,
+                                                     const uint32_t *__restrict__ bitmap, int32_t *cnt) {
     const unsigned lane = lane_id();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ns; i += warps) {
-        const int32_t v = S[i];
-        const int32_t a = row_ptr[v], e = row_ptr[v + 1];
-        int32_t cnt = 0;
-        for (int32_t base = a; base < e; base += 32) {
-            const int32_t j = base + (int32_t)lane;
-            const bool in = j < e && member(bitmap, __ldg(col + j));
-            cnt += __popc(__ballot_sync(0xffffffffu, in));
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+        const int2 ch = chunks[c];
+        const int32_t v = S[ch.x];
+        const int32_t a = row_ptr[v] + ch.y;
+        const int32_t e = min(row_ptr[v + 1], a + kChunk);
+        int32_t total = 0;
+        for (int32_t base = a; base < e; base += 32 * kChunkUnroll) {
+            int32_t w[kChunkUnroll];
+#pragma unroll
+            for (int u = 0; u < kChunkUnroll; ++u) {
+                const int32_t j = base + 32 * u + (int32_t)lane;
+                w[u] = j < e ? __ldg(col + j) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < kChunkUnroll; ++u) {
+                const bool in = w[u] >= 0 && member(bitmap, w[u]);
+                total += __popc(__ballot_sync(0xffffffffu, in));
+            }
         }
-        if (lane == 0) deg[i] = cnt;
+        if (lane == 0) cnt[c] = total;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) deg[ns] = 0;  // the scan turns it into the total
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[C] = 0;  // the scan turns it into the total
 }
 
-// Induced rows with local ids (position of the neighbour in sorted S).
-__global__ void __launch_bounds__(256) k_sub_fill(const int32_t *__restrict__ row_ptr,
-                                                  const int32_t *__restrict__ col,
-                                                  const int32_t *__restrict__ S, int32_t ns,
-                                                  const uint32_t *__restrict__ bitmap,
-                                                  const int32_t *__restrict__ sub_rp, int32_t *__restrict__ sub_col) {
+// Induced rows with local ids (position of the neighbour in sorted S): chunk c
+// writes from pos[c] on; the first chunk of row i also sets sub_rp[i].
+__global__ void __launch_bounds__(256) k_chunk_fill(const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col,
+                                                    const int32_t *__restrict__ S, int32_t ns,
+                                                    const int2 *__restrict__ chunks, int32_t C,
+                                                    const uint32_t *__restrict__ bitmap,
+                                                    const int32_t *__restrict__ pos, int32_t *__restrict__ sub_rp,
+                                                    int32_t *__restrict__ sub_col) {
     const unsigned lane = lane_id();
     const unsigned below = (1u << lane) - 1u;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ns; i += warps) {
-        const int32_t v = S[i];
-        const int32_t a = row_ptr[v], e = row_ptr[v + 1];
-        int32_t out = sub_rp[i];
-        for (int32_t base = a; base < e; base += 32) {
-            const int32_t j = base + (int32_t)lane;
-            const int32_t w = j < e ? __ldg(col + j) : 0;
-            const bool in = j < e && member(bitmap, w);
-            const unsigned bal = __ballot_sync(0xffffffffu, in);
-            if (in) {
-                int32_t lo = 0, hi = ns;  // first index with S[idx] >= w (w is in S)
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi) >> 1;
-                    if (__ldg(S + mid) < w)
-                        lo = mid + 1;
-                    else
-                        hi = mid;
-                }
-                sub_col[out + __popc(bal & below)] = lo;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < C; c += warps) {
+        const int2 ch = chunks[c];
+        const int32_t v = S[ch.x];
+        const int32_t a = row_ptr[v] + ch.y;
+        const int32_t e = min(row_ptr[v + 1], a + kChunk);
+        int32_t out = pos[c];
+        if (ch.y == 0 && lane == 0) sub_rp[ch.x] = out;
+        for (int32_t base = a; base < e; base += 32 * kChunkUnroll) {
+            int32_t w[kChunkUnroll];
+#pragma unroll
+            for (int u = 0; u < kChunkUnroll; ++u) {
+                const int32_t j = base + 32 * u + (int32_t)lane;
+                w[u] = j < e ? __ldg(col + j) : -1;
             }
-            out += __popc(bal);
+#pragma unroll
+            for (int u = 0; u < kChunkUnroll; ++u) {
+                const bool in = w[u] >= 0 && member(bitmap, w[u]);
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (in) {
+                    int32_t lo = 0, hi = ns;  // first index with S[idx] >= w (w is in S)
+                    while (lo < hi) {
+                        const int32_t mid = (lo + hi) >> 1;
+                        if (__ldg(S + mid) < w[u])
+                            lo = mid + 1;
+                        else
+                            hi = mid;
+                    }
+                    sub_col[out + __popc(bal & below)] = lo;
+                }
+                out += __popc(bal);
+            }
         }
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sub_rp[ns] = pos[C];
 }
 
 int warp_grid(int64_t items) {
@@ -267,6 +298,10 @@ struct Req {
     pg_request r{};
     std::vector<int32_t> S;  // subgraph: sorted, deduplicated
     int64_t U = 0;           // subgraph: sum of the full degrees of S (bound on the induced entries)
+    std::vector<int2> chunks;  // subgraph: phase-1 work, (index in S, first entry of the row)
+    bool zc = false;               // pairs: the caller's buffers are page-locked, the GPU uses them directly
+    const int32_t *d_pairs = nullptr;  // pairs: device-visible input and outputs (arena, or the caller's)
+    float *d_cn = nullptr, *d_jac = nullptr;
     St st = St::Queued;
     size_t a_off = 0, a_len = 0;  // arena block
     size_t p_off = 0, p_len = 0;  // staging block
@@ -278,11 +313,12 @@ struct Req {
     Clock::time_point t_submit, t_admit;
 };
 
-// Arena layout of a subgraph request: phase 1 [S | sub_rp | scan | sub_col | tc], then phase 2.
+// Arena layout of a subgraph request: phase 1 [S | chunks | cnt/pos | scan |
+// sub_rp | sub_col | tc], then phase 2.
 struct SubLayout {
-    size_t S, rp, scan, col, tc, p2, total_p1;
+    size_t S, chunks, pos, scan, rp, col, tc, p2, total_p1;
 };
-SubLayout sub_layout(int64_t ns, int64_t U) {
+SubLayout sub_layout(int64_t ns, int64_t C, int64_t U) {
     SubLayout L{};
     size_t o = 0;
     auto take = [&](size_t b) {
@@ -291,14 +327,20 @@ SubLayout sub_layout(int64_t ns, int64_t U) {
         return at;
     };
     L.S = take(4 * (size_t)ns);
+    L.chunks = take(8 * (size_t)C);
+    L.pos = take(4 * ((size_t)C + 1));
+    L.scan = take(scan_scratch_bytes(C + 1));
     L.rp = take(4 * ((size_t)ns + 1));
-    L.scan = take(scan_scratch_bytes(ns + 1));
     L.col = take(4 * (size_t)U + 4);
     L.tc = take(sizeof(pg_tc_result));
     L.p2 = o;
     L.total_p1 = o;
     return L;
 }
+// Staging of a subgraph request: [S | chunks | out], out = nnz (int32) at +0
+// and the pg_tc_result at +64.
+size_t sub_pin_out(const Req *r) { return round_up(4 * r->S.size(), 256) + round_up(8 * r->chunks.size(), 256); }
+
 // Phase 2: [index | sketch | build | table | hist] or [index | exact].
 struct Phase2 {
     size_t index, sketch, build, table, hist, exact, total;
@@ -350,6 +392,8 @@ struct pg_server {
     cudaStream_t pair_stream = nullptr;
     std::vector<cudaStream_t> sub_streams;
     cudaEvent_t iter_ev[2] = {nullptr, nullptr};
+    cudaEvent_t kern_ev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // timing around the pair kernel
+    bool kern_timed[2] = {false, false};
     int64_t iter_id[2] = {-1, -1};
     bool iter_busy[2] = {false, false};
     int64_t iters = 0;
@@ -373,7 +417,7 @@ namespace {
 void fill_opts(const pg_server_opts *in, pg_server_opts *o) {
     if (in) *o = *in;
     if (o->streams <= 0) o->streams = 4;
-    if (o->max_inflight <= 0) o->max_inflight = 1024;
+    if (o->max_inflight <= 0) o->max_inflight = 4096;
     if (o->iteration_pairs <= 0) o->iteration_pairs = 262144;
     if (o->pinned_bytes == 0) o->pinned_bytes = 256ull << 20;
     if (o->sub_bits == 0) o->sub_bits = 512;
@@ -405,8 +449,8 @@ void finish(pg_server *sv, Req *r, pg_status status) {
     resp.kind = r->r.kind;
     resp.count = r->r.kind == PG_REQ_SUBGRAPH_TC ? (int64_t)r->S.size() : r->r.count;
     if (status == PG_OK && r->r.kind == PG_REQ_SUBGRAPH_TC && r->nnz > 0)
-        std::memcpy(&resp.tc, sv->pinned + r->p_off + round_up(4 * r->S.size(), 256) + 64, sizeof(pg_tc_result));
-    if (status == PG_OK && r->r.kind == PG_REQ_PAIRS) {
+        std::memcpy(&resp.tc, sv->pinned + r->p_off + sub_pin_out(r) + 64, sizeof(pg_tc_result));
+    if (status == PG_OK && r->r.kind == PG_REQ_PAIRS && !r->zc) {
         const size_t P = (size_t)r->r.count;
         const uint8_t *out = sv->pinned + r->p_off + round_up(8 * P, 256);
         if (r->r.cn) std::memcpy(r->r.cn, out, 4 * P);
@@ -436,41 +480,45 @@ void finish(pg_server *sv, Req *r, pg_status status) {
 void request_bytes(const pg_server *sv, const Req *r, size_t *arena, size_t *pinned) {
     if (r->r.kind == PG_REQ_PAIRS) {
         const size_t P = (size_t)r->r.count;
-        *arena = round_up(8 * P, 256) + 2 * round_up(4 * P, 256);
-        *pinned = round_up(8 * P, 256) + 2 * round_up(4 * P, 256);
+        *arena = r->zc ? 0 : round_up(8 * P, 256) + 2 * round_up(4 * P, 256);
+        *pinned = *arena;
     } else {
         const int64_t ns = (int64_t)r->S.size();
-        const SubLayout L = sub_layout(ns, r->U);
+        const SubLayout L = sub_layout(ns, (int64_t)r->chunks.size(), r->U);
         *arena = L.total_p1 + phase2_layout((int32_t)ns, r->U, r->r.estimator, sv->opts.sub_bits).total;
-        *pinned = round_up(4 * (size_t)ns, 256) + 256;
+        *pinned = sub_pin_out(r) + 256;
     }
 }
 
 pg_status launch_phase1(pg_server *sv, Req *r) {
     const int32_t ns = (int32_t)r->S.size();
+    const int32_t C = (int32_t)r->chunks.size();
     cudaStream_t s = sv->sub_streams[r->stream];
     uint8_t *base = sv->arena + r->a_off;
-    const SubLayout L = sub_layout(ns, r->U);
+    const SubLayout L = sub_layout(ns, C, r->U);
     int32_t *S = reinterpret_cast<int32_t *>(base + L.S);
-    int32_t *rp = reinterpret_cast<int32_t *>(base + L.rp);
+    const int2 *chunks = reinterpret_cast<const int2 *>(base + L.chunks);
+    int32_t *pos = reinterpret_cast<int32_t *>(base + L.pos);
     int32_t *scan = reinterpret_cast<int32_t *>(base + L.scan);
+    int32_t *rp = reinterpret_cast<int32_t *>(base + L.rp);
     int32_t *col = reinterpret_cast<int32_t *>(base + L.col);
     uint32_t *bm = sv->bitmaps[r->stream];
+    // staging [S | chunks | out] has the arena's [S | chunks] offsets: one copy
     uint8_t *pin = sv->pinned + r->p_off;
-    std::memcpy(pin, r->S.data(), 4 * (size_t)ns);
-    PG_TRY_CUDA(cudaMemcpyAsync(S, pin, 4 * (size_t)ns, cudaMemcpyHostToDevice, s), "subgraph: copy S");
+    std::memcpy(pin + L.S, r->S.data(), 4 * (size_t)ns);
+    std::memcpy(pin + L.chunks, r->chunks.data(), 8 * (size_t)C);
+    PG_TRY_CUDA(cudaMemcpyAsync(base, pin, L.chunks + 8 * (size_t)C, cudaMemcpyHostToDevice, s), "subgraph: copy S");
     const int tg = (int)std::min<int64_t>((ns + 255) / 256, 4LL * device_info().sm_count);
     k_mark<<<tg, 256, 0, s>>>(S, ns, bm, 1);
-    k_sub_degree<<<warp_grid(ns), 256, 0, s>>>(sv->g.row_ptr, sv->g.col, S, ns, bm, rp);
+    k_chunk_count<<<warp_grid(C), 256, 0, s>>>(sv->g.row_ptr, sv->g.col, S, chunks, C, bm, pos);
     note_launch(2);
     PG_TRY_CUDA(cudaGetLastError(), "subgraph: degrees");
-    PG_TRY_CUDA(launch_exclusive_scan(rp, (int64_t)ns + 1, scan, s), "subgraph: scan");
-    k_sub_fill<<<warp_grid(ns), 256, 0, s>>>(sv->g.row_ptr, sv->g.col, S, ns, bm, rp, col);
+    PG_TRY_CUDA(launch_exclusive_scan(pos, (int64_t)C + 1, scan, s), "subgraph: scan");
+    k_chunk_fill<<<warp_grid(C), 256, 0, s>>>(sv->g.row_ptr, sv->g.col, S, ns, chunks, C, bm, pos, rp, col);
     k_mark<<<tg, 256, 0, s>>>(S, ns, bm, 0);
     note_launch(2);
     PG_TRY_CUDA(cudaGetLastError(), "subgraph: induced rows");
-    const size_t out = round_up(4 * (size_t)ns, 256);
-    PG_TRY_CUDA(cudaMemcpyAsync(pin + out, rp + ns, 4, cudaMemcpyDeviceToHost, s), "subgraph: copy size");
+    PG_TRY_CUDA(cudaMemcpyAsync(pin + sub_pin_out(r), rp + ns, 4, cudaMemcpyDeviceToHost, s), "subgraph: copy size");
     PG_TRY_CUDA(cudaEventRecord(r->ev, s), "subgraph: event");
     return PG_OK;
 }
@@ -479,7 +527,7 @@ pg_status launch_phase2(pg_server *sv, Req *r) {
     const int32_t ns = (int32_t)r->S.size();
     cudaStream_t s = sv->sub_streams[r->stream];
     uint8_t *base = sv->arena + r->a_off;
-    const SubLayout L = sub_layout(ns, r->U);
+    const SubLayout L = sub_layout(ns, (int64_t)r->chunks.size(), r->U);
     const Phase2 P = phase2_layout(ns, r->nnz, r->r.estimator, sv->opts.sub_bits);
     uint8_t *b2 = base + L.p2;
     const int32_t *rp = reinterpret_cast<const int32_t *>(base + L.rp);
@@ -512,24 +560,49 @@ pg_status launch_phase2(pg_server *sv, Req *r) {
                     "subgraph: pass");
         PG_TRY_CUDA(launch_tc_finalize(hist, sk, r->r.estimator, tc, s), "subgraph: finalize");
     }
-    uint8_t *pin = sv->pinned + r->p_off + round_up(4 * (size_t)ns, 256);
+    uint8_t *pin = sv->pinned + r->p_off + sub_pin_out(r);
     PG_TRY_CUDA(cudaMemcpyAsync(pin + 64, tc, sizeof(pg_tc_result), cudaMemcpyDeviceToHost, s), "subgraph: copy");
     PG_TRY_CUDA(cudaEventRecord(r->ev, s), "subgraph: event");
     return PG_OK;
 }
 
+// Copies of whole request blocks between staging and arena, merged where
+// consecutive blocks are adjacent in both (the allocators hand out blocks in
+// order, so a burst of admissions usually becomes one copy).
+struct Span {
+    size_t p, a, len;
+};
+cudaError_t copy_spans(pg_server *sv, std::vector<Span> &spans, cudaMemcpyKind kind) {
+    std::sort(spans.begin(), spans.end(), [](const Span &x, const Span &y) { return x.p < y.p; });
+    size_t i = 0;
+    while (i < spans.size()) {
+        Span cur = spans[i++];
+        while (i < spans.size() && spans[i].p == cur.p + cur.len && spans[i].a == cur.a + cur.len)
+            cur.len += spans[i++].len;
+        cudaError_t e = kind == cudaMemcpyHostToDevice
+                            ? cudaMemcpyAsync(sv->arena + cur.a, sv->pinned + cur.p, cur.len, kind, sv->pair_stream)
+                            : cudaMemcpyAsync(sv->pinned + cur.p, sv->arena + cur.a, cur.len, kind, sv->pair_stream);
+        if (e != cudaSuccess) return e;
+    }
+    spans.clear();
+    return cudaSuccess;
+}
+
 // Admit queued requests in order while they fit. Caller holds mu.
 bool admit(pg_server *sv) {
     bool progress = false;
+    std::vector<Span> h2d;
+    std::vector<Req *> admitted_pairs;
     while (!sv->queue.empty() &&
-           (int64_t)(sv->pairs_active.size() + sv->subs_active.size()) < sv->opts.max_inflight) {
+           (int64_t)(sv->pairs_active.size() + sv->subs_active.size() + admitted_pairs.size()) <
+               sv->opts.max_inflight) {
         Req *r = sv->reqs[sv->queue.front()];
         size_t need_a = 0, need_p = 0;
         request_bytes(sv, r, &need_a, &need_p);
         size_t a_off = 0, p_off = 0;
-        if (!sv->arena_alloc.alloc(need_a, &a_off)) break;
-        if (!sv->pinned_alloc.alloc(need_p, &p_off)) {
-            sv->arena_alloc.release(a_off, need_a);
+        if (need_a && !sv->arena_alloc.alloc(need_a, &a_off)) break;
+        if (need_p && !sv->pinned_alloc.alloc(need_p, &p_off)) {
+            if (need_a) sv->arena_alloc.release(a_off, need_a);
             break;
         }
         sv->queue.pop_front();
@@ -539,20 +612,21 @@ bool admit(pg_server *sv) {
         r->p_len = need_p;
         r->t_admit = Clock::now();
         progress = true;
-        if (r->r.kind == PG_REQ_PAIRS) {
-            r->st = St::Phase1;
+        r->st = St::Phase1;
+        if (r->r.kind == PG_REQ_PAIRS && r->zc) {
+            admitted_pairs.push_back(r);
+        } else if (r->r.kind == PG_REQ_PAIRS) {
+            // block layout [pairs | cn | jac], identical in staging and arena; the whole block is
+            // copied (the output parts are overwritten by the kernel)
             const size_t P = (size_t)r->r.count;
             std::memcpy(sv->pinned + p_off, r->r.data, 8 * P);
-            cudaError_t e = cudaMemcpyAsync(sv->arena + a_off, sv->pinned + p_off, 8 * P, cudaMemcpyHostToDevice,
-                                            sv->pair_stream);
-            if (e != cudaSuccess) {
-                sv->failed = cuda_status(e, "serve: copy pairs");
-                finish(sv, r, sv->failed);
-                continue;
-            }
-            sv->pairs_active.push_back(r);
+            h2d.push_back(Span{p_off, a_off, round_up(need_a, 256)});
+            uint8_t *a = sv->arena + a_off;
+            r->d_pairs = reinterpret_cast<const int32_t *>(a);
+            r->d_cn = r->r.cn ? reinterpret_cast<float *>(a + round_up(8 * P, 256)) : nullptr;
+            r->d_jac = r->r.jac ? reinterpret_cast<float *>(a + round_up(8 * P, 256) + round_up(4 * P, 256)) : nullptr;
+            admitted_pairs.push_back(r);
         } else {
-            r->st = St::Phase1;
             r->stream = sv->rr++ % (int)sv->sub_streams.size();
             cudaError_t e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
             pg_status st = e == cudaSuccess ? launch_phase1(sv, r) : cuda_status(e, "serve: event");
@@ -565,6 +639,13 @@ bool admit(pg_server *sv) {
             sv->stats.subgraphs++;
         }
     }
+    const cudaError_t e = h2d.empty() ? cudaSuccess : copy_spans(sv, h2d, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        sv->failed = cuda_status(e, "serve: copy pairs");
+        for (Req *r : admitted_pairs) finish(sv, r, sv->failed);
+        return true;
+    }
+    for (Req *r : admitted_pairs) sv->pairs_active.push_back(r);
     return progress;
 }
 
@@ -592,13 +673,11 @@ bool launch_pairs(pg_server *sv) {
         grabbed = false;
         for (Req *r : sv->pairs_active) {
             if (r->next >= r->r.count) continue;
-            const size_t P = (size_t)r->r.count;
-            uint8_t *a = sv->arena + r->a_off;
             const int32_t take = (int32_t)std::min<int64_t>(kTile, r->r.count - r->next);
             PairTile t{};
-            t.pairs = reinterpret_cast<const int32_t *>(a);
-            t.cn = r->r.cn ? reinterpret_cast<float *>(a + round_up(8 * P, 256)) : nullptr;
-            t.jac = r->r.jac ? reinterpret_cast<float *>(a + round_up(8 * P, 256) + round_up(4 * P, 256)) : nullptr;
+            t.pairs = r->d_pairs;
+            t.cn = r->d_cn;
+            t.jac = r->d_jac;
             t.begin = (int32_t)r->next;
             t.count = take;
             t.est = r->r.estimator;
@@ -633,35 +712,49 @@ bool launch_pairs(pg_server *sv) {
             int64_t grid = (warps + kServeThreads / 32 - 1) / (kServeThreads / 32);
             const int64_t cap = 8LL * device_info().sm_count;
             if (grid > cap) grid = cap;
+            e = cudaEventRecord(sv->kern_ev[slot][0], s);
             k_serve_pairs<<<(unsigned)grid, kServeThreads, 0, s>>>(sv->g.row_ptr, sv->g.n, sv->desc_dev[slot],
                                                                    (int32_t)nt, sk);
             note_launch();
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(sv->kern_ev[slot][1], s);
+            sv->kern_timed[slot] = e == cudaSuccess;
             sv->stats.pair_launches++;
         }
     }
     for (Req *r : exact) {
         if (e != cudaSuccess) break;
-        const size_t P = (size_t)r->r.count;
-        uint8_t *a = sv->arena + r->a_off;
         EdgeOutputs eo{};
-        eo.cn = r->r.cn ? reinterpret_cast<float *>(a + round_up(8 * P, 256)) : nullptr;
-        eo.jac = r->r.jac ? reinterpret_cast<float *>(a + round_up(8 * P, 256) + round_up(4 * P, 256)) : nullptr;
-        e = launch_exact_pairs(sv->g.row_ptr, sv->g.col, sv->g.n, EdgeIndex{}, reinterpret_cast<const int32_t *>(a),
-                               (int64_t)P, eo, s);
+        eo.cn = r->d_cn;
+        eo.jac = r->d_jac;
+        e = launch_exact_pairs(sv->g.row_ptr, sv->g.col, sv->g.n, EdgeIndex{}, r->d_pairs, r->r.count, eo, s);
     }
-    // results of the requests that end in this launch go back to the staging memory
-    for (Req *r : sv->pairs_active) {
-        if (e != cudaSuccess) break;
-        if (r->last_iter != id) continue;
-        const size_t P = (size_t)r->r.count;
-        const size_t o = round_up(8 * P, 256);
-        if (r->r.cn) e = cudaMemcpyAsync(sv->pinned + r->p_off + o, sv->arena + r->a_off + o, 4 * P,
-                                         cudaMemcpyDeviceToHost, s);
-        const size_t o2 = o + round_up(4 * P, 256);
-        if (e == cudaSuccess && r->r.jac)
-            e = cudaMemcpyAsync(sv->pinned + r->p_off + o2, sv->arena + r->a_off + o2, 4 * P,
+    // results of the requests that end in this launch go back to the staging memory: from the
+    // output part of a block to its end, merged across blocks adjacent in both staging and arena
+    // (a merged copy also brings back the pair part of the inner blocks, unchanged)
+    if (e == cudaSuccess) {
+        struct Out {
+            size_t p, a, out, len;  // block offsets, start of its outputs, block bytes
+        };
+        std::vector<Out> d2h;
+        for (Req *r : sv->pairs_active) {
+            if (r->last_iter != id || r->zc || (!r->r.cn && !r->r.jac)) continue;
+            d2h.push_back(Out{r->p_off, r->a_off, round_up(8 * (size_t)r->r.count, 256), round_up(r->a_len, 256)});
+        }
+        std::sort(d2h.begin(), d2h.end(), [](const Out &x, const Out &y) { return x.p < y.p; });
+        size_t i = 0;
+        while (i < d2h.size() && e == cudaSuccess) {
+            const Out first = d2h[i++];
+            size_t end_p = first.p + first.len, end_a = first.a + first.len;
+            while (i < d2h.size() && d2h[i].p == end_p && d2h[i].a == end_a) {
+                end_p += d2h[i].len;
+                end_a += d2h[i].len;
+                ++i;
+            }
+            const size_t from = first.out;
+            e = cudaMemcpyAsync(sv->pinned + first.p + from, sv->arena + first.a + from, end_p - first.p - from,
                                 cudaMemcpyDeviceToHost, s);
+        }
     }
     if (e == cudaSuccess) e = cudaEventRecord(sv->iter_ev[slot], s);
     if (e != cudaSuccess) {
@@ -685,6 +778,12 @@ bool poll_events(pg_server *sv) {
         if (st != PG_OK) sv->failed = st;
         const int64_t id = sv->iter_id[slot];
         sv->iter_busy[slot] = false;
+        if (sv->kern_timed[slot] && st == PG_OK) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, sv->kern_ev[slot][0], sv->kern_ev[slot][1]) == cudaSuccess)
+                sv->stats.pair_kernel_ns += (uint64_t)(ms * 1e6);
+            sv->kern_timed[slot] = false;
+        }
         std::vector<Req *> keep;
         for (Req *r : sv->pairs_active) {
             if (r->last_iter == id && r->next >= r->r.count)
@@ -710,7 +809,7 @@ bool poll_events(pg_server *sv) {
         }
         if (r->st == St::Phase1) {
             int32_t nnz = 0;
-            std::memcpy(&nnz, sv->pinned + r->p_off + round_up(4 * r->S.size(), 256), 4);
+            std::memcpy(&nnz, sv->pinned + r->p_off + sub_pin_out(r), 4);
             r->nnz = nnz;
             if (nnz <= 0 || sv->failed) {
                 r->nnz = 0;
@@ -718,7 +817,7 @@ bool poll_events(pg_server *sv) {
                 continue;
             }
             // keep phase 1 and the exact phase-2 size, give the rest back
-            const SubLayout L = sub_layout((int64_t)r->S.size(), r->U);
+            const SubLayout L = sub_layout((int64_t)r->S.size(), (int64_t)r->chunks.size(), r->U);
             const size_t need = L.total_p1 + phase2_layout((int32_t)r->S.size(), r->nnz, r->r.estimator,
                                                            sv->opts.sub_bits).total;
             sv->arena_alloc.shrink(r->a_off, r->a_len, need);
@@ -854,6 +953,8 @@ pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, in
         if (e == cudaSuccess) sv->sub_streams.push_back(s);
     }
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&sv->iter_ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        for (int j = 0; j < 2 && e == cudaSuccess; ++j) e = cudaEventCreate(&sv->kern_ev[i][j]);
     cudaStream_t s0 = sv->pair_stream;
     if (e == cudaSuccess) {
         for (int i = 0; i < o.streams; ++i) launch_fill_u64(reinterpret_cast<uint64_t *>(sv->bitmaps[i]), bm_bytes / 8, 0, s0);
@@ -874,6 +975,9 @@ pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, in
         if (sv->pair_stream) cudaStreamDestroy(sv->pair_stream);
         for (auto ev : sv->iter_ev)
             if (ev) cudaEventDestroy(ev);
+        for (auto &pr : sv->kern_ev)
+            for (auto ev : pr)
+                if (ev) cudaEventDestroy(ev);
         if (sv->pinned) cudaFreeHost(sv->pinned);
         delete sv;
         return cuda_status(e, "pg_server_create");
@@ -886,66 +990,189 @@ pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, in
     return PG_OK;
 }
 
-pg_status pg_submit(pg_server *sv, const pg_request *req, uint64_t *ticket) {
-    PG_REQUIRE(sv && req && ticket, PG_ERR_INVALID_ARG, "pg_submit: NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Device address of a page-locked host range [p, p + bytes), if the whole
+// range is one mapping of page-locked memory the device can reach.
+bool device_view(const void *p, size_t bytes, void **dev) {
+    cudaPointerAttributes a0{}, a1{};
+    const char *last = static_cast<const char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();  // clear the error the failed query recorded
+        return false;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+        return false;
+    if (static_cast<char *>(a1.devicePointer) - static_cast<char *>(a0.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return false;
+    *dev = a0.devicePointer;
+    return true;
+}
+
+// Validate one request and build its record (no lock held).
+pg_status prepare(pg_server *sv, const pg_request *req, Req **out) {
+    PG_REQUIRE(req, PG_ERR_INVALID_ARG, "pg_submit: NULL request");
     PG_REQUIRE(req->kind == PG_REQ_PAIRS || req->kind == PG_REQ_SUBGRAPH_TC, PG_ERR_INVALID_ARG,
                "pg_submit: unknown request kind %d", req->kind);
     PG_REQUIRE(req->count >= 0 && req->count < (1LL << 31) && (req->count == 0 || req->data), PG_ERR_INVALID_ARG,
                "pg_submit: count %lld with data %p", (long long)req->count, (const void *)req->data);
-    Req *r = new Req();
-    r->r = *req;
-    r->t_submit = Clock::now();
     if (req->kind == PG_REQ_PAIRS) {
         const int32_t est = req->estimator;
         const bool ok = est == PG_EST_EXACT || ((est == PG_EST_BF_AND || est == PG_EST_BF_L) && sv->has_bf) ||
                         (est == PG_EST_KH && sv->has_kh);
-        if (!ok) {
-            delete r;
-            return set_error(PG_ERR_UNSUPPORTED, "pg_submit: pair estimator %d needs a resident sketch of its kind",
-                             est);
-        }
+        PG_REQUIRE(ok, PG_ERR_UNSUPPORTED, "pg_submit: pair estimator %d needs a resident sketch of its kind", est);
     } else {
-        if (req->estimator != PG_EST_BF_AND && req->estimator != PG_EST_BF_L && req->estimator != PG_EST_EXACT) {
-            delete r;
-            return set_error(PG_ERR_UNSUPPORTED, "pg_submit: subgraph estimator %d (BF_AND, BF_L or EXACT)",
-                             req->estimator);
+        PG_REQUIRE(req->estimator == PG_EST_BF_AND || req->estimator == PG_EST_BF_L || req->estimator == PG_EST_EXACT,
+                   PG_ERR_UNSUPPORTED, "pg_submit: subgraph estimator %d (BF_AND, BF_L or EXACT)", req->estimator);
+        for (int64_t i = 0; i < req->count; ++i)
+            PG_REQUIRE(req->data[i] >= 0 && req->data[i] < sv->g.n, PG_ERR_INVALID_ARG,
+                       "pg_submit: vertex %d outside [0, %d)", req->data[i], sv->g.n);
+    }
+    Req *r = new Req();
+    r->r = *req;
+    r->t_submit = Clock::now();
+    if (req->kind == PG_REQ_PAIRS && req->count > 0) {
+        // page-locked input and outputs: the kernel reads and writes them in place (over the
+        // CPU-GPU link), with no staging copies; anything else goes through the staging memory
+        void *dp = nullptr, *dc = nullptr, *dj = nullptr;
+        const size_t P = (size_t)req->count;
+        r->zc = device_view(req->data, 8 * P, &dp) && (!req->cn || device_view(req->cn, 4 * P, &dc)) &&
+                (!req->jac || device_view(req->jac, 4 * P, &dj));
+        if (r->zc) {
+            r->d_pairs = static_cast<const int32_t *>(dp);
+            r->d_cn = static_cast<float *>(dc);
+            r->d_jac = static_cast<float *>(dj);
         }
+    }
+    if (req->kind == PG_REQ_SUBGRAPH_TC) {
         r->S.assign(req->data, req->data + req->count);
-        for (int32_t v : r->S)
-            if (v < 0 || v >= sv->g.n) {
-                delete r;
-                return set_error(PG_ERR_INVALID_ARG, "pg_submit: vertex %d outside [0, %d)", v, sv->g.n);
-            }
         std::sort(r->S.begin(), r->S.end());
         r->S.erase(std::unique(r->S.begin(), r->S.end()), r->S.end());
-        for (int32_t v : r->S) r->U += sv->deg[v];
+        r->chunks.reserve(r->S.size());
+        for (size_t i = 0; i < r->S.size(); ++i) {
+            const int32_t d = sv->deg[r->S[i]];
+            r->U += d;
+            int32_t off = 0;
+            do {
+                r->chunks.push_back(make_int2((int32_t)i, off));
+                off += kChunk;
+            } while (off < d);
+        }
     }
+    *out = r;
+    return PG_OK;
+}
+
+// Queue a prepared request (mu held).
+pg_status enqueue_locked(pg_server *sv, Req *r, uint64_t *ticket) {
     size_t need_a = 0, need_p = 0;
     request_bytes(sv, r, &need_a, &need_p);
-    std::lock_guard<std::mutex> lk(sv->mu);
-    if (sv->failed != PG_OK || sv->stop) {
-        const pg_status f = sv->failed != PG_OK ? sv->failed : PG_ERR_CANCELLED;
-        delete r;
-        return set_error(f, "pg_submit: the server has stopped");
-    }
-    if (round_up(need_a, 256) > sv->arena_alloc.size() || round_up(need_p, 256) > sv->pinned_alloc.size()) {
-        delete r;
-        return set_error(PG_ERR_NO_MEMORY, "pg_submit: request needs %zu arena and %zu staging bytes, the server "
-                         "has %zu and %zu", need_a, need_p, sv->arena_alloc.size(), sv->pinned_alloc.size());
-    }
+    if (sv->failed != PG_OK || sv->stop)
+        return set_error(sv->failed != PG_OK ? sv->failed : PG_ERR_CANCELLED, "pg_submit: the server has stopped");
+    if (round_up(need_a, 256) > sv->arena_alloc.size() || round_up(need_p, 256) > sv->pinned_alloc.size())
+        return set_error(PG_ERR_NO_MEMORY,
+                         "pg_submit: request needs %zu arena and %zu staging bytes, the server has %zu and %zu",
+                         need_a, need_p, sv->arena_alloc.size(), sv->pinned_alloc.size());
     r->ticket = sv->next_ticket++;
     *ticket = r->ticket;
     sv->stats.submitted++;
     sv->reqs[r->ticket] = r;
-    const bool empty = (req->kind == PG_REQ_PAIRS && req->count == 0) ||
-                       (req->kind == PG_REQ_SUBGRAPH_TC && r->S.empty());
-    if (empty) {
+    const bool empty = (r->r.kind == PG_REQ_PAIRS && r->r.count == 0) ||
+                       (r->r.kind == PG_REQ_SUBGRAPH_TC && r->S.empty());
+    if (empty)
         finish(sv, r, PG_OK);
-        return PG_OK;
+    else
+        sv->queue.push_back(r->ticket);
+    return PG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pg_status pg_submit(pg_server *sv, const pg_request *req, uint64_t *ticket) {
+    PG_REQUIRE(sv && ticket, PG_ERR_INVALID_ARG, "pg_submit: NULL argument");
+    Req *r = nullptr;
+    pg_status st = prepare(sv, req, &r);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    st = enqueue_locked(sv, r, ticket);
+    if (st) {
+        delete r;
+        return st;
     }
-    sv->queue.push_back(r->ticket);
     sv->cv_work.notify_one();
     return PG_OK;
+}
+
+pg_status pg_submit_many(pg_server *sv, const pg_request *reqs, int64_t count, uint64_t *tickets) {
+    PG_REQUIRE(sv && tickets && count >= 0 && (count == 0 || reqs), PG_ERR_INVALID_ARG,
+               "pg_submit_many: NULL argument");
+    std::vector<Req *> rs((size_t)count, nullptr);
+    for (int64_t i = 0; i < count; ++i) {
+        const pg_status st = prepare(sv, reqs + i, &rs[i]);
+        if (st) {
+            for (Req *r : rs) delete r;
+            return set_error(st, "pg_submit_many: request %lld: %s", (long long)i, pg_last_error());
+        }
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int64_t i = 0; i < count; ++i) {
+        size_t need_a = 0, need_p = 0;
+        request_bytes(sv, rs[i], &need_a, &need_p);
+        if (round_up(need_a, 256) > sv->arena_alloc.size() || round_up(need_p, 256) > sv->pinned_alloc.size() ||
+            sv->failed != PG_OK || sv->stop) {
+            const pg_status f = sv->failed != PG_OK ? sv->failed : sv->stop ? PG_ERR_CANCELLED : PG_ERR_NO_MEMORY;
+            for (Req *r : rs) delete r;
+            return set_error(f, "pg_submit_many: request %lld can not be served (%s)", (long long)i,
+                             pg_status_string(f));
+        }
+    }
+    for (int64_t i = 0; i < count; ++i) {
+        const pg_status st = enqueue_locked(sv, rs[i], tickets + i);  // cannot fail after the checks above
+        if (st) delete rs[i];
+    }
+    sv->cv_work.notify_one();
+    return PG_OK;
+}
+
+pg_status pg_poll_many(pg_server *sv, const uint64_t *tickets, int64_t count, pg_response *out, int64_t timeout_us,
+                       int64_t *n_done) {
+    PG_REQUIRE(sv && count >= 0 && (count == 0 || (tickets && out)), PG_ERR_INVALID_ARG,
+               "pg_poll_many: NULL argument");
+    std::unique_lock<std::mutex> lk(sv->mu);
+    const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+    std::vector<char> got((size_t)count, 0);
+    int64_t done = 0;
+    for (;;) {
+        for (int64_t i = 0; i < count; ++i) {
+            if (got[i]) continue;
+            auto it = sv->done.find(tickets[i]);
+            if (it != sv->done.end()) {
+                out[i] = it->second;
+                sv->done.erase(it);
+                got[i] = 1;
+                ++done;
+            } else if (sv->reqs.find(tickets[i]) == sv->reqs.end()) {
+                out[i] = pg_response{};
+                out[i].status = PG_ERR_NOT_FOUND;
+                got[i] = 1;
+                ++done;
+            }
+        }
+        if (done == count || timeout_us <= 0 || Clock::now() >= deadline) break;
+        sv->cv_done.wait_until(lk, deadline);
+    }
+    for (int64_t i = 0; i < count; ++i)
+        if (!got[i]) {
+            out[i] = pg_response{};
+            out[i].status = PG_ERR_BUSY;
+        }
+    if (n_done) *n_done = done;
+    return done == count ? PG_OK : set_error(PG_ERR_BUSY, "pg_poll_many: %lld of %lld complete", (long long)done,
+                                             (long long)count);
 }
 
 pg_status pg_poll(pg_server *sv, uint64_t ticket, pg_response *out, int64_t timeout_us) {
@@ -1022,6 +1249,9 @@ pg_status pg_server_destroy(pg_server *sv) {
     }
     for (auto ev : sv->iter_ev)
         if (ev) cudaEventDestroy(ev);
+    for (auto &pr : sv->kern_ev)
+        for (auto ev : pr)
+            if (ev) cudaEventDestroy(ev);
     if (sv->pinned) cudaFreeHost(sv->pinned);
     for (auto &kv : sv->reqs) delete kv.second;
     delete sv;

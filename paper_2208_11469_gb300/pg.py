@@ -34,8 +34,8 @@ SYMBOLS = [
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
-    "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_poll", "pg_cancel", "pg_server_stats_get",
-    "pg_server_destroy",
+    "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_submit_many", "pg_poll_many", "pg_poll",
+    "pg_cancel", "pg_server_stats_get", "pg_server_destroy",
 ]
 REQ_PAIRS, REQ_SUBGRAPH_TC = 1, 2
 
@@ -89,10 +89,24 @@ class Response(ctypes.Structure):
                 ("tc", TcResult), ("queue_us", ctypes.c_double), ("total_us", ctypes.c_double)]
 
 
+def _np_dtypes():
+    import numpy as np
+    req = np.dtype([("kind", "<i4"), ("estimator", "<i4"), ("count", "<i8"), ("data", "<u8"), ("cn", "<u8"),
+                    ("jac", "<u8")])
+    resp = np.dtype([("status", "<i4"), ("kind", "<i4"), ("count", "<i8"), ("edges", "<u8"),
+                     ("count_sum", "<u8"), ("exact_tc", "<u8"), ("reserved", "<u8"), ("est_tc", "<f8"),
+                     ("est_tc_alt", "<f8"), ("queue_us", "<f8"), ("total_us", "<f8")])
+    assert req.itemsize == ctypes.sizeof(Request) and resp.itemsize == ctypes.sizeof(Response)
+    return req, resp
+
+
+REQUEST_DTYPE, RESPONSE_DTYPE = _np_dtypes()
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [(nm, ctypes.c_uint64) for nm in
                 ("submitted", "completed", "cancelled", "failed", "pair_launches", "pairs", "subgraphs", "queued",
-                 "running", "arena_used", "arena_peak", "arena_bytes")]
+                 "running", "arena_used", "arena_peak", "arena_bytes", "pair_kernel_ns")]
 
 
 TC_RESULT_BYTES = 48
@@ -147,6 +161,8 @@ def lib() -> ctypes.CDLL:
                 "pg_server_create": (i32, [P(Csr), P(P(SketchDesc)), i32, vp, sz, P(ServerOpts), P(vp)]),
                 "pg_submit": (i32, [vp, P(Request), P(ctypes.c_uint64)]),
                 "pg_poll": (i32, [vp, ctypes.c_uint64, P(Response), i64]),
+                "pg_submit_many": (i32, [vp, vp, i64, vp]),
+                "pg_poll_many": (i32, [vp, vp, i64, vp, i64, P(i64)]),
                 "pg_cancel": (i32, [vp, ctypes.c_uint64]),
                 "pg_server_stats_get": (i32, [vp, P(ServerStats)]),
                 "pg_server_destroy": (i32, [vp]),
@@ -525,6 +541,16 @@ class Batch:
 
 
 # ------------------------------------------------------------------ serving
+def pinned_empty(shape, dtype):
+    """A numpy array in page-locked host memory: a view of a pinned torch
+    tensor, which the array's base keeps alive."""
+    import numpy as np
+    dt = np.dtype(dtype)
+    n = int(np.prod(shape))
+    t = torch.empty(max(n * dt.itemsize, 16), dtype=torch.uint8, pin_memory=True)
+    return t.numpy()[: n * dt.itemsize].view(dt).reshape(shape)
+
+
 class Server:
     """pg_server_*: a request loop over the resident graph `g` and its
     sketches (see include/pg.h). Requests take and return host numpy arrays;
@@ -579,6 +605,82 @@ class Server:
         _check(lib().pg_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "pg_submit")
         self._live[t.value] = (v, None, None)
         return t.value
+
+    def submit_pairs_many(self, pairs, offsets, est: int, want_cn: bool = True, want_jac: bool = True,
+                          pinned: bool = False):
+        """Many pair requests in one call: request i is pairs[offsets[i]:offsets[i+1]]
+        (pairs int32 [P, 2]). Returns (tickets uint64 [R], cn float32 [P] or None,
+        jac float32 [P] or None); request i's outputs are the same slice.
+        pinned=True puts the outputs in page-locked memory; with a page-locked
+        `pairs` too (pinned_empty), the GPU reads and writes them in place."""
+        import numpy as np
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        offsets = np.asarray(offsets, dtype=np.int64)
+        R = offsets.size - 1
+        alloc = (lambda k: pinned_empty(k, np.float32)) if pinned else (lambda k: np.empty(k, np.float32))
+        cn = alloc(max(pairs.shape[0], 1)) if want_cn else None
+        jac = alloc(max(pairs.shape[0], 1)) if want_jac else None
+        reqs = np.zeros(R, dtype=REQUEST_DTYPE)
+        counts = np.diff(offsets)
+        reqs["kind"] = REQ_PAIRS
+        reqs["estimator"] = est
+        reqs["count"] = counts
+        nz = counts > 0
+        reqs["data"] = np.where(nz, pairs.ctypes.data + 8 * offsets[:-1], 0)
+        if cn is not None:
+            reqs["cn"] = np.where(nz, cn.ctypes.data + 4 * offsets[:-1], 0)
+        if jac is not None:
+            reqs["jac"] = np.where(nz, jac.ctypes.data + 4 * offsets[:-1], 0)
+        tickets = np.zeros(R, dtype=np.uint64)
+        _check(lib().pg_submit_many(self._h, reqs.ctypes.data, R, tickets.ctypes.data), "pg_submit_many")
+        keep = (pairs, cn, jac)
+        for t in tickets.tolist():
+            self._live[t] = keep
+        return tickets, cn, jac
+
+    def submit_many(self, reqs_list):
+        """Mixed requests in one call: a list of ("pairs", int32 [P, 2], est) or
+        ("sub", int32 vertices, est). Pair outputs are returned per request in
+        the response of poll_many via `outputs`. Returns (tickets, outputs)."""
+        import numpy as np
+        R = len(reqs_list)
+        reqs = np.zeros(R, dtype=REQUEST_DTYPE)
+        outputs, keep = [], []
+        for i, (kind, x, est) in enumerate(reqs_list):
+            if kind == "pairs":
+                x = np.ascontiguousarray(x, dtype=np.int32).reshape(-1, 2)
+                cn = np.empty(max(x.shape[0], 1), np.float32)
+                jac = np.empty(max(x.shape[0], 1), np.float32)
+                reqs[i] = (REQ_PAIRS, est, x.shape[0], x.ctypes.data if x.shape[0] else 0,
+                           cn.ctypes.data if x.shape[0] else 0, jac.ctypes.data if x.shape[0] else 0)
+                outputs.append((cn[: x.shape[0]], jac[: x.shape[0]]))
+                keep.append((x, cn, jac))
+            else:
+                x = np.ascontiguousarray(x, dtype=np.int32).reshape(-1)
+                reqs[i] = (REQ_SUBGRAPH_TC, est, x.size, x.ctypes.data if x.size else 0, 0, 0)
+                outputs.append(None)
+                keep.append((x, None, None))
+        tickets = np.zeros(R, dtype=np.uint64)
+        _check(lib().pg_submit_many(self._h, reqs.ctypes.data, R, tickets.ctypes.data), "pg_submit_many")
+        for t, k in zip(tickets.tolist(), keep):
+            self._live[t] = k
+        return tickets, outputs
+
+    def poll_many(self, tickets, timeout_us: int = 0):
+        """Responses (numpy structured array, RESPONSE_DTYPE) of the tickets;
+        status -8 for those still running after timeout_us."""
+        import numpy as np
+        tickets = np.ascontiguousarray(tickets, dtype=np.uint64)
+        out = np.zeros(tickets.size, dtype=RESPONSE_DTYPE)
+        nd = ctypes.c_int64()
+        st = lib().pg_poll_many(self._h, tickets.ctypes.data, tickets.size, out.ctypes.data, int(timeout_us),
+                                ctypes.byref(nd))
+        if st not in (0, -8):
+            _check(st, "pg_poll_many")
+        for t, s_ in zip(tickets.tolist(), out["status"].tolist()):
+            if s_ != -8:
+                self._live.pop(t, None)
+        return out
 
     def poll(self, ticket: int, timeout_us: int = 0):
         """The response as a dict (with 'cn'/'jac' arrays for pairs), or None

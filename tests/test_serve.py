@@ -261,3 +261,78 @@ def test_bad_requests(pg, world):
         assert r["status"] == 0 and r["tc"]["edges"] == 0 and r["tc"]["est_tc"] == 0.0
     finally:
         sv.close()
+
+
+@pytest.mark.gpu
+def test_submit_many_equals_single_calls(pg, world):
+    """A burst through pg_submit_many / pg_poll_many: every answer equals the
+    single-call answer, the pair launches take many requests each, and the
+    concatenated form (one pair array, per-request slices) gives the same."""
+    sv = pg.Server(world["g"], [world["bf"], world["kh"]], 512 << 20)
+    rng = np.random.default_rng(17)
+    try:
+        items = []
+        for i in range(300):
+            if i % 50 == 7:
+                j = int(rng.integers(0, world["cl"].size))
+                v = int(np.searchsorted(world["rp"], j, side="right") - 1)
+                items.append(("sub", synth.bfs_ball(world["rp"], world["cl"], v, 3000), pg.EST_BF_AND))
+            else:
+                P = int(np.clip(round(rng.lognormal(np.log(64), 1.5)), 1, 65536))
+                items.append(("pairs", _pairs(world, P, 500 + i), [pg.EST_BF_AND, pg.EST_KH][i % 2]))
+        l0 = sv.stats()["pair_launches"]
+        tickets, outs = sv.submit_many(items)
+        resp = sv.poll_many(tickets, timeout_us=60_000_000)
+        assert (resp["status"] == 0).all()
+        assert sv.stats()["pair_launches"] - l0 < 100  # requests share launches
+        for (kind, x, est), r, o in zip(items, resp, outs):
+            if kind == "pairs":
+                want = _want_pairs(pg, world, x, est)
+                np.testing.assert_array_equal(o[0], want[0])
+                np.testing.assert_array_equal(o[1], want[1])
+            else:
+                want = _want_subgraph(pg, world, x, est)
+                assert (r["edges"], r["count_sum"], r["est_tc"]) == (want["edges"], want["count_sum"], want["est_tc"])
+        # the concatenated form
+        pl = [x for k, x, _ in items if k == "pairs"]
+        offs = np.concatenate([[0], np.cumsum([p.shape[0] for p in pl])])
+        t2, cn, jac = sv.submit_pairs_many(np.concatenate(pl), offs, pg.EST_BF_L)
+        r2 = sv.poll_many(t2, timeout_us=60_000_000)
+        assert (r2["status"] == 0).all() and (r2["count"] == np.diff(offs)).all()
+        want = _want_pairs(pg, world, np.concatenate(pl), pg.EST_BF_L)
+        np.testing.assert_array_equal(cn[: offs[-1]], want[0])
+        np.testing.assert_array_equal(jac[: offs[-1]], want[1])
+        # unknown tickets come back as not found, without waiting
+        r3 = sv.poll_many(np.array([10 ** 9], np.uint64), timeout_us=1000)
+        assert r3["status"][0] == -7
+    finally:
+        sv.close()
+
+
+@pytest.mark.gpu
+def test_page_locked_buffers_are_used_in_place(pg, world):
+    """Pair requests whose input and outputs are page-locked skip the staging
+    copies and the arena (the kernel reads and writes them over the CPU-GPU
+    link); answers are the same as through the staging path."""
+    sv = pg.Server(world["g"], [world["bf"], world["kh"]], 64 << 20)
+    try:
+        sizes = [1, 5, 700, 3000, 20000]
+        host = np.concatenate([_pairs(world, P, 900 + i, invalid=(P > 4)) for i, P in enumerate(sizes)])
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        pinned = pg.pinned_empty(host.shape, np.int32)
+        pinned[...] = host
+        peak0 = sv.stats()["arena_used"]
+        for est in (pg.EST_BF_AND, pg.EST_KH, pg.EST_EXACT):
+            t, cn, jac = sv.submit_pairs_many(pinned, offs, est, pinned=True)
+            r = sv.poll_many(t, timeout_us=60_000_000)
+            assert (r["status"] == 0).all()
+            want = _want_pairs(pg, world, host, est)
+            np.testing.assert_array_equal(cn[: offs[-1]], want[0])
+            np.testing.assert_array_equal(jac[: offs[-1]], want[1])
+            # the same requests through the staging path
+            t2, cn2, jac2 = sv.submit_pairs_many(host, offs, est)
+            assert (sv.poll_many(t2, timeout_us=60_000_000)["status"] == 0).all()
+            np.testing.assert_array_equal(cn2[: offs[-1]], want[0])
+        assert sv.stats()["arena_used"] == peak0
+    finally:
+        sv.close()
