@@ -72,6 +72,7 @@ def lib():
                 "pgo_khash_pairs": (None, [vp, i32, vp, vp, i64, vp]),
                 "pgo_onehash_pairs": (None, [vp, i32, u32, vp, vp, vp, i64, vp, vp, vp]),
                 "pgo_hash_array": (None, [u32, u32, vp, i64, vp]),
+                "pgo_components": (None, [i32, i64, vp, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -384,3 +385,44 @@ def analyze(row_ptr, col, est: int, *, l=256, b=2, k=16, seed=1, sk=None):
     elif est == EST_EXACT:
         out["tc_exact"] = int(c.sum()) // 3
     return out
+
+
+# --------------------------------------------------------------------------
+# Jarvis-Patrick clustering (Sec. III-B, Listing "Jarvis-Patrick clustering")
+# --------------------------------------------------------------------------
+
+def components(n: int, eu, ev, keep) -> np.ndarray:
+    """Label of every vertex = the smallest vertex id of its connected
+    component in (V, {e : keep[e]})."""
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    keep = np.ascontiguousarray(keep, dtype=np.uint8)
+    label = np.empty(n, dtype=np.int32)
+    lib().pgo_components(n, eu.size, _p(eu), _p(ev), _p(keep), _p(label))
+    return label
+
+
+def jp_keep(row_ptr, est: int, counts: dict, pu, pv, tau: float, *, l=256, b=2, k=16) -> np.ndarray:
+    """The Listing's test |N_u ∩ N_v|^ > tau per edge, evaluated on the double
+    estimate of each estimator (reading P)."""
+    e = pair_estimates(row_ptr, est, counts, pu, pv, l=l, b=b, k=k)
+    return e > tau
+
+
+def jarvis_patrick(row_ptr, col, est: int, tau: float, *, l=256, b=2, k=16, seed=1, sk=None):
+    """Clusters = connected components of the graph restricted to the edges
+    whose (estimated) common-neighbour count exceeds tau. Returns a dict
+    with labels (smallest vertex id per cluster), the number of clusters
+    (singletons included), the kept-edge mask and the upper edges."""
+    rp, cl = _csr(row_ptr, col)
+    n = rp.size - 1
+    kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_KH: "khash", EST_1H: "onehash",
+            EST_1H_LITERAL: "onehash"}.get(est)
+    if sk is None and kind is not None:
+        sk = sketch(rp, cl, kind, l=l, b=b, k=k, seed=seed)
+    eu, ev = upper_edges(rp, cl)
+    counts = pair_counts(rp, cl, est, sk, eu, ev, seed=seed)
+    keep = jp_keep(rp, est, counts, eu, ev, tau, l=l, b=b, k=k)
+    label = components(n, eu, ev, keep)
+    return {"labels": label, "clusters": int(np.count_nonzero(label == np.arange(n))),
+            "kept": int(np.count_nonzero(keep)), "keep": keep, "eu": eu, "ev": ev, "counts": counts}

@@ -316,3 +316,30 @@ void pgo_hash_array(uint32_t seed, uint32_t i, const int32_t *x, int64_t cnt, ui
 {
     for (int64_t t = 0; t < cnt; ++t) out[t] = pgo_hash(seed, i, x[t]);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Connected components of a subset of the edges (Jarvis-Patrick clustering,  */
+/* Sec. III-B, Listing "Jarvis-Patrick clustering": the clusters are the      */
+/* connected components of (V, C), C = edges whose |N_u ∩ N_v| exceeds tau).  */
+/* ------------------------------------------------------------------------ */
+
+static int32_t uf_find(int32_t *parent, int32_t x)
+{
+    while (parent[x] != x) x = parent[x];
+    return x;
+}
+
+/* label[v] = smallest vertex id of v's component in the graph (V, {e : keep[e]}),
+ * by serial union-find that always makes the smaller root the parent. */
+void pgo_components(int32_t n, int64_t m, const int32_t *eu, const int32_t *ev, const uint8_t *keep,
+                    int32_t *label)
+{
+    for (int32_t v = 0; v < n; ++v) label[v] = v;
+    for (int64_t e = 0; e < m; ++e) {
+        if (!keep[e]) continue;
+        int32_t a = uf_find(label, eu[e]), b = uf_find(label, ev[e]);
+        if (a == b) continue;
+        if (a < b) label[b] = a; else label[a] = b;
+    }
+    for (int32_t v = 0; v < n; ++v) label[v] = uf_find(label, v);
+}
