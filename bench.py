@@ -1,7 +1,7 @@
 """Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096|serve22]
+                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096|serve22|jp22]
                     [--impl ours|reference]
 
 A step is one pass of the whole sketched path over the synthetic graph of the
@@ -20,10 +20,12 @@ time is the maximum over ranks and the value the sum of the ranks' work.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
 import re
+import struct
 import subprocess
 import sys
 import threading
@@ -56,6 +58,9 @@ WORKLOADS = {
     # serving: resident R-MAT scale 22, edge factor 16, Bloom 512 bits b = 2 and k-Hash k = 32 on the
     # device; pair requests of lognormal size (median 256, sigma 2, clipped to 1..65536), half existing
     # edges and half random pairs, and induced-subgraph triangle counts of BFS balls of 10^U(3,6) edges
+    # Jarvis-Patrick clustering on R-MAT scale 22, edge factor 16: Bloom at 25% (b = 2) and k-Hash k = 32,
+    # threshold tau = 4 common neighbours; exact clustering as the comparison
+    "jp22": dict(jp=True, gen=("rmat", 22, 16, 22), budget=0.25, b=2, khash=32, tau=4.0),
     "serve22": dict(serve=True, gen=("rmat", 22, 16, 22), bits=512, b=2, khash=32, pair_requests=2000,
                     subgraph_requests=12, subgraph_share=0.02),
 }
@@ -91,7 +96,7 @@ def generate(workload: str, device):
     from paper_2208_11469_gb300 import synth
     if "batch" in WORKLOADS[workload]:
         return generate_batch(workload, device)
-    if "serve" in WORKLOADS[workload]:
+    if "serve" in WORKLOADS[workload] or "jp" in WORKLOADS[workload]:
         kind, scale, ef, seed = WORKLOADS[workload]["gen"]
         return synth.rmat(scale, ef, seed=seed, device=device)
     kind, *a = WORKLOADS[workload]["gen"]
@@ -616,6 +621,112 @@ def run_batch(args, ws, rank, dev):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ clustering
+def run_jp(args, ws, rank, dev):
+    """Jarvis-Patrick: one step = edge index, sketch build and the
+    clustering pass (counts, keep test, union-find, labels) per sketch."""
+    from paper_2208_11469_gb300 import pg
+    w = WORKLOADS[args.workload]
+    rp, cl = generate(args.workload, dev)
+    g = pg.graph(rp, cl, build_index=True)
+    bits = pg.bloom_bits_for_budget(w["budget"], g.n, g.nnz)
+    bws = torch.empty(max(pg.build_workspace_bytes(g), 16), dtype=torch.uint8, device=dev)
+    bf = pg.alloc_sketch(g, pg.SK_BLOOM, bits=bits, b=w["b"], seed=1)
+    kh = pg.alloc_sketch(g, pg.SK_KHASH, k=w["khash"], seed=1)
+    passes = [("bloom", bf, pg.EST_BF_AND), ("khash", kh, pg.EST_KH)]
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    res = {nm: torch.zeros(32, dtype=torch.uint8, device=dev) for nm, _, _ in passes}
+    jws = {nm: torch.empty(max(pg.lib().pg_jarvis_patrick_workspace_bytes(ctypes.byref(g.csr()),
+                                                                         ctypes.byref(sk.desc()), est), 16),
+                           dtype=torch.uint8, device=dev) for nm, sk, est in passes}
+    names = ["index"] + ["build_" + p[0] for p in passes] + ["jp_" + p[0] for p in passes]
+
+    def step(ev=None):
+        s = torch.cuda.current_stream()
+
+        def mark(nm, i):
+            if ev is not None:
+                ev[nm][i].record(s)
+        mark("index", 0)
+        pg.build_edge_index_into(g)
+        mark("index", 1)
+        for nm, sk, est in passes:
+            mark("build_" + nm, 0)
+            if sk.kind == pg.SK_BLOOM:
+                pg.build_bloom(g, sk.bits, sk.b, sk.seed, out=sk, workspace=bws)
+            else:
+                pg.build_minhash(g, sk.kind, sk.k, sk.seed, out=sk, workspace=bws)
+            mark("build_" + nm, 1)
+        for nm, sk, est in passes:
+            mark("jp_" + nm, 0)
+            pg.jarvis_patrick(g, sk, est, w["tau"], labels=labels, ws=jws[nm], out=res[nm], read=False)
+            mark("jp_" + nm, 1)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
+           for _ in range(args.steps)]
+    l0 = pg.kernel_launches()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        a.record()
+        for i in range(args.steps):
+            step(evs[i])
+        b_.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = pg.kernel_launches() - l0
+    ms = max_over_ranks(a.elapsed_time(b_) / args.steps, ws, dev)
+    per = {nm: float(np.mean([e[nm][0].elapsed_time(e[nm][1]) for e in evs])) for nm in names}
+    out = {}
+    for nm, _, _ in passes:
+        c, k_, e_, _ = struct.unpack("<qqqq", bytes(res[nm].cpu().numpy().tobytes()))
+        out[nm] = {"clusters": c, "kept": k_, "edges": e_}
+    # the exact clustering
+    ex = None
+    if not args.no_exact:
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        _, exr = pg.jarvis_patrick(g, None, pg.EST_EXACT, w["tau"], want_labels=False)
+        eb.record()
+        torch.cuda.synchronize()
+        ex = dict(exr, ms=ea.elapsed_time(eb))
+        for nm in out:
+            out[nm]["relative_cluster_count"] = out[nm]["clusters"] / max(exr["clusters"], 1)
+    m = g.m
+    peak, peak_kind = peaks()
+    dom = max((p[0] for p in passes), key=lambda nm: per["jp_" + nm])
+    sk_dom = [p[1] for p in passes if p[0] == dom][0]
+    payload = sk_dom.bits / 8 if sk_dom.kind == pg.SK_BLOOM else 4 * sk_dom.k
+    # count pass (row of v, v, degrees for MinHash, count out) + union pass (count, u, v, degrees)
+    alg = m * (payload + 4 + (8 if sk_dom.kind != pg.SK_BLOOM else 0) + 4) + g.n * (payload + 12) + m * 20 + g.n * 8
+    achieved = alg / (per["jp_" + dom] * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, e, desc = oracle_sample(rp, cl, dict(w, onehash=None), bits, target_s=15.0)
+        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+    if rank == 0:
+        line = {
+            "metric": METRIC + " (Jarvis-Patrick)", "value": m * len(passes) * ws / (ms * 1e-3),
+            "unit": "intersections/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded on-device generator)",
+            "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "m": m, "bloom_bits": bits,
+                       "bloom_b": w["b"], "khash_k": w["khash"], "tau": w["tau"],
+                       "l2": "inputs larger than L2, no flush", "parallelism": f"replicas x{ws}"},
+            "phases_ms": per,
+            "roofline": {"bound": "hbm", "kernel": f"pg_jarvis_patrick ({dom}: count pass + union-find)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes": alg, "peak_source": peak_kind},
+            "e2e": None, "gpu_launches": launches, "clocks": clk.summary(), "results": out, "exact_gpu": ex,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- serving
 def serve_requests(workload, rp, cl, seed=7):
     """The request set: pair requests (sizes lognormal, half edges and half
@@ -932,8 +1043,9 @@ def main():
     from paper_2208_11469_gb300 import pg
 
     dev = torch.device("cuda", local)
-    if "batch" in WORKLOADS[args.workload] or "serve" in WORKLOADS[args.workload]:
-        (run_batch if "batch" in WORKLOADS[args.workload] else run_serve)(args, ws, rank, dev)
+    special = [k for k in ("batch", "serve", "jp") if k in WORKLOADS[args.workload]]
+    if special:
+        {"batch": run_batch, "serve": run_serve, "jp": run_jp}[special[0]](args, ws, rank, dev)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return

@@ -283,6 +283,31 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
 pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *index, const pg_sketch *sk,
                                     int32_t estimator, pg_tc_result *out, pg_stream_t stream);
 
+/* ----------------------------------------------------- Jarvis-Patrick --
+ * Jarvis-Patrick clustering (Sec. III-B, Listing "Jarvis-Patrick
+ * clustering"): the edges (u, v) whose common-neighbour count |N_u ∩ N_v|
+ * exceeds tau form the clustering C; the clusters are the connected
+ * components of (V, C), singletons included. The count is exact
+ * (PG_EST_EXACT, sk NULL) or estimated with sk (every estimator). Keep test:
+ * exact count > tau; Bloom AND: the AND estimate of the count > tau (decided
+ * on the count, the estimate being non-decreasing in it); Bloom L: count / b
+ * > tau; MinHash: J / (1 + J) * (d_u + d_v) > tau, J = c / K, in double.
+ *   labels: DEVICE int32 [n] or NULL: each vertex's cluster, named by the
+ *           smallest vertex id in it (the same for any execution order)
+ *   out:    DEVICE pg_jp_result
+ *   workspace: pg_jarvis_patrick_workspace_bytes; index: pg_build_edge_index.
+ * Errors as pg_triangle_count, plus PG_ERR_INVALID_ARG for a NaN tau. */
+typedef struct pg_jp_result {
+    int64_t clusters; /* connected components of (V, C) */
+    int64_t kept;     /* |C| */
+    int64_t edges;    /* undirected edges of the graph */
+    int64_t reserved;
+} pg_jp_result;
+size_t pg_jarvis_patrick_workspace_bytes(const pg_csr *g, const pg_sketch *sk, int32_t estimator);
+pg_status pg_jarvis_patrick(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                            double tau, void *workspace, size_t workspace_bytes, int32_t *labels,
+                            pg_jp_result *out, pg_stream_t stream);
+
 /* ---------------------------------------------------------------- batch --
  * Many small graphs analysed together (the per-graph Bloom-filter triangle
  * count of Sec. V, Eq. bf_int, and the LCC of Sec. II-B, per graph), in one

@@ -33,6 +33,7 @@ SYMBOLS = [
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
+    "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
     "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_submit_many", "pg_poll_many", "pg_poll",
     "pg_cancel", "pg_server_stats_get", "pg_server_destroy",
@@ -151,6 +152,8 @@ def lib() -> ctypes.CDLL:
                 "pg_kernel_launches": (ctypes.c_uint64, []),
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
                 "pg_triangle_count_noalloc": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, vp]),
+                "pg_jarvis_patrick_workspace_bytes": (sz, [P(Csr), P(SketchDesc), i32]),
+                "pg_jarvis_patrick": (i32, [P(Csr), vp, P(SketchDesc), i32, ctypes.c_double, vp, sz, vp, vp, vp]),
                 "pg_batch_autotune": (i32, [vp, vp, i32, ctypes.c_double, P(BatchConfig)]),
                 "pg_batch_workspace_bytes": (sz, [P(Csr), i32, vp, P(BatchConfig)]),
                 "pg_batch_create": (i32, [P(Csr), i32, vp, P(BatchConfig), u32, vp, sz, vp, vp, vp, vp,
@@ -459,6 +462,28 @@ def triangle_count_noalloc(g: Graph, sk: Sketch, est: int, *, out: torch.Tensor 
     _check(lib().pg_triangle_count_noalloc(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(out), _stream()),
            "pg_triangle_count_noalloc")
     return read_tc_result(out) if read else out
+
+
+# ------------------------------------------------------------ Jarvis-Patrick
+def jarvis_patrick(g: Graph, sk: Sketch | None, est: int, tau: float, *, labels: torch.Tensor | None = None,
+                   want_labels: bool = True, ws: torch.Tensor | None = None, out: torch.Tensor | None = None,
+                   read: bool = True):
+    """pg_jarvis_patrick: returns (labels int32 [n] or None, result dict or
+    the device result buffer when read=False)."""
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    if ws is None:
+        ws = _dev_bytes(lib().pg_jarvis_patrick_workspace_bytes(ctypes.byref(c), dref, est), g.device)
+    if want_labels and labels is None:
+        labels = torch.empty(max(g.n, 1), dtype=torch.int32, device=g.device)
+    out = out if out is not None else torch.zeros(32, dtype=torch.uint8, device=g.device)
+    _check(lib().pg_jarvis_patrick(ctypes.byref(c), _ptr(g.index), dref, est, float(tau), _ptr(ws), ws.numel(),
+                                   _ptr(labels) if want_labels else None, _ptr(out), _stream()),
+           "pg_jarvis_patrick")
+    if not read:
+        return (labels[: g.n] if want_labels else None), out
+    clusters, kept, edges, _ = struct.unpack("<qqqq", bytes(out.cpu().numpy().tobytes()))
+    return (labels[: g.n] if want_labels else None), {"clusters": clusters, "kept": kept, "edges": edges}
 
 
 # -------------------------------------------------------------------- batch
