@@ -33,6 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
+EST_BF_OR, EST_BF_SS = 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -73,6 +74,8 @@ def lib():
                 "pgo_onehash_pairs": (None, [vp, i32, u32, vp, vp, vp, i64, vp, vp, vp]),
                 "pgo_hash_array": (None, [u32, u32, vp, i64, vp]),
                 "pgo_components": (None, [i32, i64, vp, vp, vp, vp]),
+                "pgo_bloom_or_ones": (i32, [vp, vp, u32]),
+                "pgo_bloom_or_pairs": (None, [vp, u32, vp, vp, i64, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -226,6 +229,16 @@ def bloom_pairs(bits: np.ndarray, pu, pv) -> np.ndarray:
     return out
 
 
+def bloom_or_pairs(bits: np.ndarray, pu, pv) -> np.ndarray:
+    """B_{X∪Y,1} = popcount(BF_u OR BF_v) per pair."""
+    bits = np.ascontiguousarray(bits, dtype=np.uint8)
+    pu = np.ascontiguousarray(pu, dtype=np.int32)
+    pv = np.ascontiguousarray(pv, dtype=np.int32)
+    out = np.empty(pu.size, dtype=np.int32)
+    lib().pgo_bloom_or_pairs(_p(bits), bits.shape[1], _p(pu), _p(pv), pu.size, _p(out))
+    return out
+
+
 def khash_pairs(M: np.ndarray, pu, pv) -> np.ndarray:
     M = np.ascontiguousarray(M, dtype=np.int32)
     pu = np.ascontiguousarray(pu, dtype=np.int32)
@@ -257,6 +270,28 @@ def est_and(ones_, l: int, b: int):
     o = np.asarray(ones_, dtype=np.float64)
     o = np.where(o == l, o - 1.0, o)
     return -(l / b) * np.log(1.0 - o / l)
+
+
+def est_or(union_ones, size_x, size_y, l: int, b: int):
+    """Eq. bf_int_union: |X| + |Y| + (l/b) log(1 - B~_{X∪Y,1}/l), the single-set
+    estimator of |X ∪ Y| subtracted from the exact |X| + |Y|; the count is
+    bounded as for AND, B~ = B - [B = l] (reading E)."""
+    o = np.asarray(union_ones, dtype=np.float64)
+    o = np.where(o == l, o - 1.0, o)
+    s = np.asarray(size_x, dtype=np.float64) + np.asarray(size_y, dtype=np.float64)
+    return s + (l / b) * np.log(1.0 - o / l)
+
+
+def est_single_set(ones_, l: int, b: int):
+    """The single-set estimator the paper analyses beside its own (Sec. VIII),
+    applied to the AND filter (reading R): |X|^ = log(1 - B~_{X,1}/l) /
+    (b log(1 - 1/l)). The printed form carries a leading minus that would make
+    it negative for every non-empty filter (both logarithms are negative); the
+    expected fill l (1 - (1 - 1/l)^{b t}) must map back to t, which fixes the
+    sign. The count is bounded as for AND."""
+    o = np.asarray(ones_, dtype=np.float64)
+    o = np.where(o == l, o - 1.0, o)
+    return np.log(1.0 - o / l) / (b * np.log(1.0 - 1.0 / l))
 
 
 def est_limit(ones_, b: int):
@@ -299,8 +334,10 @@ def pair_counts(row_ptr, col, est: int, sk, pu, pv, *, seed=1):
     for 1-Hash, 'K' and 'c_lit'; for exact, |N_u ∩ N_v|."""
     if est == EST_EXACT:
         return {"count": exact_pairs(row_ptr, col, pu, pv)}
-    if est in (EST_BF_AND, EST_BF_L):
+    if est in (EST_BF_AND, EST_BF_L, EST_BF_SS):
         return {"count": bloom_pairs(sk, pu, pv)}
+    if est == EST_BF_OR:
+        return {"count": bloom_pairs(sk, pu, pv), "union": bloom_or_pairs(sk, pu, pv)}
     if est == EST_KH:
         return {"count": khash_pairs(sk, pu, pv)}
     if est in (EST_1H, EST_1H_LITERAL):
@@ -319,6 +356,10 @@ def pair_estimates(row_ptr, est: int, counts: dict, pu, pv, *, l=256, b=2, k=16)
         return est_and(c, l, b)
     if est == EST_BF_L:
         return est_limit(c, b)
+    if est == EST_BF_OR:
+        return est_or(counts["union"], d[pu], d[pv], l, b)
+    if est == EST_BF_SS:
+        return est_single_set(c, l, b)
     if est == EST_KH:
         return est_minhash(c, np.full(len(c), k), d[pu], d[pv])
     if est == EST_1H:
@@ -327,6 +368,23 @@ def pair_estimates(row_ptr, est: int, counts: dict, pu, pv, *, l=256, b=2, k=16)
         # the formula as printed: J = |M1_X ∩ M1_Y| / k
         return est_minhash(counts["c_lit"], np.full(len(c), k), d[pu], d[pv])
     raise ValueError(est)
+
+
+def similarities(row_ptr, estimate, pu, pv):
+    """Listing sim: with I = clamp(|N_u ∩ N_v|^, 0, min(d_u, d_v)) (reading F),
+    Jaccard I / (d_u + d_v - I), overlap I / min(d_u, d_v) and total
+    neighbours d_u + d_v - I; common neighbours = the estimate itself. A
+    quotient with a zero denominator is 0."""
+    d = degrees(row_ptr).astype(np.float64)
+    du, dv = d[pu], d[pv]
+    cn = np.asarray(estimate, dtype=np.float64)
+    I = np.clip(cn, 0.0, np.minimum(du, dv))
+    den = du + dv - I
+    mn = np.minimum(du, dv)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        J = np.where(den > 0, I / np.where(den > 0, den, 1.0), 0.0)
+        ov = np.where(mn > 0, I / np.where(mn > 0, mn, 1.0), 0.0)
+    return {"cn": cn, "jac": J, "overlap": ov, "total": du + dv - I}
 
 
 def jaccard_and_cn(row_ptr, estimate, pu, pv):
@@ -353,8 +411,8 @@ def analyze(row_ptr, col, est: int, *, l=256, b=2, k=16, seed=1, sk=None):
     per-edge CN and Jaccard, and the integer histograms of the counts."""
     rp, cl = _csr(row_ptr, col)
     n = rp.size - 1
-    kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_KH: "khash", EST_1H: "onehash",
-            EST_1H_LITERAL: "onehash"}.get(est)
+    kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_BF_OR: "bloom", EST_BF_SS: "bloom", EST_KH: "khash",
+            EST_1H: "onehash", EST_1H_LITERAL: "onehash"}.get(est)
     if sk is None and kind is not None:
         sk = sketch(rp, cl, kind, l=l, b=b, k=k, seed=seed)
     eu, ev = upper_edges(rp, cl)
@@ -374,9 +432,15 @@ def analyze(row_ptr, col, est: int, *, l=256, b=2, k=16, seed=1, sk=None):
         "tc": float(e.sum()) / 3.0, "S": S, "T": T, "lcc": lcc, "cn": cn, "jac": J,
         "sketch": sk,
     }
+    sim = similarities(rp, e, eu, ev)
+    out["overlap"], out["total"] = sim["overlap"], sim["total"]
     c = np.asarray(counts["count"], dtype=np.int64)
-    if est in (EST_BF_AND, EST_BF_L):
+    if est in (EST_BF_AND, EST_BF_L, EST_BF_SS):
         out["hist"] = np.bincount(c, minlength=l + 1).astype(np.uint64)
+    elif est == EST_BF_OR:
+        U = np.asarray(counts["union"], dtype=np.int64)
+        out["hist"] = np.concatenate([np.bincount(U, minlength=l + 1),
+                                      [int((d[eu] + d[ev]).sum())]]).astype(np.uint64)
     elif est == EST_KH:
         out["hist"] = np.bincount(c, minlength=k + 1).astype(np.uint64)
         hd = np.zeros(k + 1, dtype=np.int64)
@@ -416,8 +480,8 @@ def jarvis_patrick(row_ptr, col, est: int, tau: float, *, l=256, b=2, k=16, seed
     (singletons included), the kept-edge mask and the upper edges."""
     rp, cl = _csr(row_ptr, col)
     n = rp.size - 1
-    kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_KH: "khash", EST_1H: "onehash",
-            EST_1H_LITERAL: "onehash"}.get(est)
+    kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_BF_OR: "bloom", EST_BF_SS: "bloom", EST_KH: "khash",
+            EST_1H: "onehash", EST_1H_LITERAL: "onehash"}.get(est)
     if sk is None and kind is not None:
         sk = sketch(rp, cl, kind, l=l, b=b, k=k, seed=seed)
     eu, ev = upper_edges(rp, cl)

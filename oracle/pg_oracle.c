@@ -120,6 +120,15 @@ int32_t pgo_bloom_and_ones(const uint8_t *BX, const uint8_t *BY, uint32_t l)
     return ones;
 }
 
+/* B_{X∪Y,1}: the number of ones of BF_X OR BF_Y, the filter of X ∪ Y
+ * (Eq. bf_int_union, the OR estimator). */
+int32_t pgo_bloom_or_ones(const uint8_t *BX, const uint8_t *BY, uint32_t l)
+{
+    int32_t ones = 0;
+    for (uint32_t p = 0; p < l; ++p) ones += (BX[p] | BY[p]);
+    return ones;
+}
+
 /* B_{X,1}: the number of ones of one filter. */
 int32_t pgo_bloom_ones(const uint8_t *BX, uint32_t l)
 {
@@ -288,6 +297,13 @@ void pgo_bloom_pairs(const uint8_t *bits, uint32_t l, const int32_t *pu,
 {
     for (int64_t p = 0; p < P; ++p)
         ones[p] = pgo_bloom_and_ones(bits + (size_t)pu[p] * l, bits + (size_t)pv[p] * l, l);
+}
+
+void pgo_bloom_or_pairs(const uint8_t *bits, uint32_t l, const int32_t *pu,
+                        const int32_t *pv, int64_t P, int32_t *ones)
+{
+    for (int64_t p = 0; p < P; ++p)
+        ones[p] = pgo_bloom_or_ones(bits + (size_t)pu[p] * l, bits + (size_t)pv[p] * l, l);
 }
 
 void pgo_khash_pairs(const int32_t *M, int32_t k, const int32_t *pu,
