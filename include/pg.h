@@ -177,12 +177,17 @@ pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *workspace
 #define PG_EST_KH          3 /* Eq. (est_int_mh), J = #{i : min_i(u) = min_i(v)} / k */
 #define PG_EST_1H          4 /* Sec. IV-D, J = c_union / K (see pg_tc_result) */
 #define PG_EST_1H_LITERAL  5 /* Sec. IV-D as printed, J = |M1_u ∩ M1_v| / k */
+#define PG_EST_BF_OR       6 /* Eq. (bf_int_union): d_u + d_v + (l/b) log(1 - U/l), U = popcount(B_u OR B_v)
+                                (read as l - 1 when U = l); per-edge aux = U; pass kernels of any width */
+#define PG_EST_BF_SS       7 /* the single-set Bloom estimator on the AND filter (Sec. VIII):
+                                log(1 - B1/l) / (b log(1 - 1/l)), B1 = l read as l - 1 */
 
 /* Graph-level result, written to a DEVICE pg_tc_result. */
 typedef struct pg_tc_result {
     uint64_t edges;      /* undirected edges (or pairs) intersected */
-    uint64_t count_sum;  /* sum over them of the integer count: popcount(AND), k-Hash
-                            matches, 1-Hash c_union, or exact |N_u ∩ N_v| */
+    uint64_t count_sum;  /* sum over them of the integer count: popcount(AND) (popcount(OR)
+                            for PG_EST_BF_OR), k-Hash matches, 1-Hash c_union, or exact
+                            |N_u ∩ N_v| */
     uint64_t exact_tc;   /* PG_EST_EXACT: the exact triangle count; else 0 */
     uint64_t reserved;
     double est_tc;       /* (1/3) sum over edges of the requested estimate (Sec. VII) */
@@ -230,10 +235,27 @@ pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *
                            void *workspace, size_t workspace_bytes, float *cn, float *jac,
                            pg_stream_t stream);
 
+/* Vertex-similarity measures of Listing sim for every pair (or every upper
+ * edge with pairs NULL), from the exact or estimated |N_u ∩ N_v|: with
+ * I = clamp(estimate, 0, min(d_u, d_v)), cn = the estimate, jac =
+ * I / (d_u + d_v - I), overlap = I / min(d_u, d_v), total = d_u + d_v - I
+ * (a zero denominator gives 0). Every pointer is a DEVICE float array [P or m]
+ * or NULL. Arguments and errors as pg_jaccard_pairs. */
+typedef struct pg_similarity {
+    float *cn;
+    float *jac;
+    float *overlap;
+    float *total;
+} pg_similarity;
+pg_status pg_similarity_pairs(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                              const int32_t *pairs, int64_t P, void *workspace, size_t workspace_bytes,
+                              const pg_similarity *out, pg_stream_t stream);
+
 /* The integer counts behind every estimate, for checking and analysis:
  * count: DEVICE int32 [m or P] or NULL — popcount(AND) / k-Hash matches /
  * 1-Hash c_union / exact |N_u ∩ N_v|; aux: DEVICE int32 [m or P] or NULL —
- * 1-Hash only: K | (c_lit << 16); hist: DEVICE uint64 [pg_hist_bins] or NULL.
+ * 1-Hash: K | (c_lit << 16), Bloom OR: popcount(B_u OR B_v), else unwritten;
+ * hist: DEVICE uint64 [pg_hist_bins] or NULL.
  * pairs as in pg_jaccard_pairs. */
 pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk,
                          int32_t estimator, const int32_t *pairs, int64_t P,
@@ -259,6 +281,8 @@ typedef struct pg_outputs {
     int32_t *edge_count;
     int32_t *edge_aux;
     uint64_t *hist;
+    float *edge_overlap;  /* float [m], as pg_similarity_pairs over all upper edges */
+    float *edge_total;    /* float [m], as pg_similarity_pairs over all upper edges */
 } pg_outputs;
 pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
                      void *workspace, size_t workspace_bytes, const pg_outputs *out,

@@ -96,6 +96,8 @@ pg_status check_estimator(const pg_sketch *sk, int32_t est) {
         case PG_EST_EXACT: return PG_OK;
         case PG_EST_BF_AND:
         case PG_EST_BF_L:
+        case PG_EST_BF_OR:
+        case PG_EST_BF_SS:
             PG_REQUIRE(sk && sk->kind == PG_SK_BLOOM, PG_ERR_INVALID_ARG,
                        "estimator %d needs a Bloom sketch", est);
             return PG_OK;
@@ -132,7 +134,7 @@ Workspace carve(const pg_csr *g, const pg_sketch *sk, int32_t est, void *base) {
         w.table = reinterpret_cast<double *>(p + off);
         off += intersect_table_bytes(sk->kind, sk->bits, sk->k);
         w.hist = reinterpret_cast<uint64_t *>(p + off);
-        off += round_up(8 * (size_t)hist_bins(sk->kind, sk->bits, sk->k), 256);
+        off += round_up(8 * (size_t)hist_bins(sk->kind, sk->bits, sk->k, est), 256);
     }
     w.S = reinterpret_cast<double *>(p + off);
     off += round_up(8 * (size_t)g->n + 8, 256);
@@ -293,7 +295,7 @@ pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *ws, size_
 
 int64_t pg_hist_bins(const pg_sketch *sk, int32_t estimator) {
     if (!sk || estimator == PG_EST_EXACT) return 0;
-    return hist_bins(sk->kind, sk->bits, sk->k);
+    return hist_bins(sk->kind, sk->bits, sk->k, estimator);
 }
 
 size_t pg_workspace_bytes(const pg_csr *g, const pg_sketch *sk, int32_t estimator) {
@@ -318,7 +320,7 @@ pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch 
                     "pg_triangle_count(exact)");
         return PG_OK;
     }
-    const size_t bins = (size_t)hist_bins(sk->kind, sk->bits, sk->k);
+    const size_t bins = (size_t)hist_bins(sk->kind, sk->bits, sk->k, estimator);
     launch_fill_u64(w.hist, bins, 0, stream);
     EdgeOutputs eo{};
     eo.hist = w.hist;
@@ -354,7 +356,7 @@ pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk,
         eo.S = S;
         if (tc) {
             eo.hist = w.hist;
-            launch_fill_u64(w.hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+            launch_fill_u64(w.hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k, estimator), 0, stream);
         }
         PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk,
                                         estimator, eo, w.table, stream),
@@ -399,6 +401,34 @@ pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *
     return PG_OK;
 }
 
+pg_status pg_similarity_pairs(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                              const int32_t *pairs, int64_t P, void *ws, size_t ws_bytes,
+                              const pg_similarity *out, pg_stream_t stream) {
+    Workspace w;
+    pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
+    if (st) return st;
+    PG_REQUIRE(out != nullptr, PG_ERR_INVALID_ARG, "pg_similarity_pairs: outputs is NULL");
+    PG_REQUIRE(((reinterpret_cast<uintptr_t>(out->cn) | reinterpret_cast<uintptr_t>(out->jac) |
+                 reinterpret_cast<uintptr_t>(out->overlap) | reinterpret_cast<uintptr_t>(out->total)) &
+                3u) == 0,
+               PG_ERR_INVALID_ARG, "misaligned output pointer");
+    EdgeOutputs eo{};
+    eo.cn = out->cn;
+    eo.jac = out->jac;
+    eo.ovl = out->overlap;
+    eo.tot = out->total;
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
+    if (estimator == PG_EST_EXACT) {
+        PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, pairs, P, eo, stream),
+                    "pg_similarity_pairs(exact)");
+    } else {
+        PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, pairs, P, *sk, estimator, eo, w.table,
+                                        stream),
+                    "pg_similarity_pairs");
+    }
+    return PG_OK;
+}
+
 pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk,
                          int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
                          size_t ws_bytes, int32_t *count, int32_t *aux, uint64_t *hist,
@@ -419,7 +449,7 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
         PG_REQUIRE((reinterpret_cast<uintptr_t>(hist) & 7u) == 0, PG_ERR_INVALID_ARG,
                    "hist must be 8-byte aligned");
         eo.hist = hist;
-        launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+        launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k, estimator), 0, stream);
     }
     PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, pairs, P, *sk, estimator,
                                     eo, w.table, stream),
@@ -440,7 +470,9 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
                    (reinterpret_cast<uintptr_t>(out->edge_cn) & 3u) == 0 &&
                    (reinterpret_cast<uintptr_t>(out->edge_jac) & 3u) == 0 &&
                    (reinterpret_cast<uintptr_t>(out->edge_count) & 3u) == 0 &&
-                   (reinterpret_cast<uintptr_t>(out->edge_aux) & 3u) == 0,
+                   (reinterpret_cast<uintptr_t>(out->edge_aux) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_overlap) & 3u) == 0 &&
+                   (reinterpret_cast<uintptr_t>(out->edge_total) & 3u) == 0,
                PG_ERR_INVALID_ARG, "misaligned output pointer");
     const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
     const int32_t *upper_off = ix.upper_off;
@@ -452,10 +484,12 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
             PG_TRY_CUDA(launch_exact_tc(g->row_ptr, g->col, g->n, g->nnz, upper_off, w.exact, S,
                                         out->tc, stream),
                         "pg_analyze(exact)");
-        if (out->edge_cn || out->edge_jac || out->edge_count) {
+        if (out->edge_cn || out->edge_jac || out->edge_count || out->edge_overlap || out->edge_total) {
             EdgeOutputs eo{};
             eo.cn = out->edge_cn;
             eo.jac = out->edge_jac;
+            eo.ovl = out->edge_overlap;
+            eo.tot = out->edge_total;
             eo.count = out->edge_count;
             PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, nullptr, 0, eo,
                                            stream),
@@ -466,12 +500,14 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
         eo.S = S;
         eo.cn = out->edge_cn;
         eo.jac = out->edge_jac;
+        eo.ovl = out->edge_overlap;
+        eo.tot = out->edge_total;
         eo.count = out->edge_count;
         eo.aux = out->edge_aux;
         uint64_t *hist = out->hist ? out->hist : (out->tc ? w.hist : nullptr);
         if (hist) {
             eo.hist = hist;
-            launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k), 0, stream);
+            launch_fill_u64(hist, (size_t)hist_bins(sk->kind, sk->bits, sk->k, estimator), 0, stream);
         }
         PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk,
                                         estimator, eo, w.table, stream),

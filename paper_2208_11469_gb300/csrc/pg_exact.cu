@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restr
                                                           int32_t n, EdgeIndex ix,
                                                           const int32_t *__restrict__ pairs,
                                                           int64_t P, int32_t *count, float *cn,
-                                                          float *jac) {
+                                                          float *jac, float *ovl, float *tot) {
     const unsigned lane = lane_id();
     const unsigned g = lane % kL;
     const int64_t group = ((int64_t)blockIdx.x * kThreads + threadIdx.x) / kL;
@@ -228,10 +228,10 @@ __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restr
         if (e < e1 && g == 0) {
             if (count) count[e] = (int32_t)c;
             if (cn) cn[e] = (float)c;
-            if (jac) {
-                const float I = (float)c, den = (float)du + (float)dv - I;
-                jac[e] = den > 0.0f ? I / den : 0.0f;
-            }
+            const float I = (float)c, den = (float)du + (float)dv - I, mn = fminf((float)du, (float)dv);
+            if (jac) jac[e] = den > 0.0f ? I / den : 0.0f;
+            if (ovl) ovl[e] = mn > 0.0f ? I / mn : 0.0f;
+            if (tot) tot[e] = den;
         }
     }
 }
@@ -283,12 +283,14 @@ cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32
         if (P > 0)
         {
             k_exact_pairs<true><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, ix, pairs, P,
-                                                                       out.count, out.cn, out.jac);
+                                                                       out.count, out.cn, out.jac, out.ovl,
+                                                                       out.tot);
             note_launch();
         }
     } else if (n > 0) {
         k_exact_pairs<false><<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, ix, nullptr, 0,
-                                                                    out.count, out.cn, out.jac);
+                                                                    out.count, out.cn, out.jac, out.ovl,
+                                                                    out.tot);
         note_launch();
     }
     return cudaGetLastError();

@@ -125,11 +125,15 @@ struct EdgeOutputs {
     double *S;          // [n] sum over incident edges of the estimate (zeroed by caller) or null
     float *cn;          // per edge/pair
     float *jac;         // per edge/pair
+    float *ovl;         // per edge/pair: overlap similarity
+    float *tot;         // per edge/pair: total-neighbour similarity
     int32_t *count;     // per edge/pair
     int32_t *aux;       // per edge/pair (1-Hash)
     uint64_t *hist;     // [bins] (zeroed by caller) or null
 };
-int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k);
+// Histogram bins of a pass: Bloom l + 1 (plus one for the OR estimator's
+// degree sum), k-Hash 2 (k + 1), 1-Hash 2 (k + 1)^2 + 2 (k + 1).
+int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k, int32_t estimator);
 size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k);
 // Enqueue the estimator-table kernel (into table_ws) and the intersection
 // kernel over every upper edge (pairs == nullptr) or over P pairs.

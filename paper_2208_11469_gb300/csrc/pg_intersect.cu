@@ -58,10 +58,13 @@ struct Params {
     double *S;
     float *cn;
     float *jac;
+    float *ovl;         // overlap similarity per edge/pair
+    float *tot;         // total-neighbour similarity per edge/pair
     int32_t *count;
     int32_t *aux;
     uint64_t *hist;
     int32_t hist_len;   // number of uint64 bins
+    int32_t want_union; // Bloom OR estimator: also count popcount(row_u OR row_v) (upper 16 bits)
 };
 
 // Per-vertex sums and per-edge estimates avoid double-precision arithmetic
@@ -100,6 +103,10 @@ __device__ __forceinline__ uint32_t lane_count(const Params &p, const uint4 (&a)
             const uint32_t w0 = 4u * idx, wl = p.l / 32u;
             c += __popc(a[q].x & b[q].x) + __popc(a[q].y & b[q].y) +
                  (w0 + 2 < wl ? __popc(a[q].z & b[q].z) + __popc(a[q].w & b[q].w) : 0u);
+            if (p.want_union)  // popcount of the OR (filter of the union), l <= 1024 < 2^16
+                c += (__popc(a[q].x | b[q].x) + __popc(a[q].y | b[q].y) +
+                      (w0 + 2 < wl ? __popc(a[q].z | b[q].z) + __popc(a[q].w | b[q].w) : 0u))
+                     << 16;
         } else {
             const uint32_t i0 = 4u * idx;
             c += (i0 + 0 < p.k && a[q].x == b[q].x) + (i0 + 1 < p.k && a[q].y == b[q].y) +
@@ -239,6 +246,42 @@ __device__ __forceinline__ void add_u_runs(double *S, int32_t key, unsigned long
     if (key >= 0 && (lane == 0 || prev != key) && val != 0ull) atomicAdd(S + key, fx_to_f64(val));
 }
 
+// Similarity outputs of one edge / pair from its estimate (Listing sim):
+// I = clamp(est, 0, min(d_u, d_v)); Jaccard I / (d_u + d_v - I), overlap
+// I / min(d_u, d_v), total neighbours d_u + d_v - I (0 for a zero denominator).
+__device__ __forceinline__ void write_sims(const Params &p, int64_t e, float est_f, int32_t du, int32_t dv) {
+    if (p.cn) p.cn[e] = est_f;
+    if (p.jac || p.ovl || p.tot) {
+        const float fu = (float)du, fv = (float)dv;
+        const float mn = fminf(fu, fv);
+        const float I = fminf(fmaxf(est_f, 0.0f), mn);
+        const float den = fu + fv - I;
+        if (p.jac) p.jac[e] = den > 0.0f ? I / den : 0.0f;
+        if (p.ovl) p.ovl[e] = mn > 0.0f ? I / mn : 0.0f;
+        if (p.tot) p.tot[e] = den;
+    }
+}
+
+__device__ __forceinline__ void write_zero(const Params &p, int64_t e) {
+    if (p.count) p.count[e] = 0;
+    if (p.aux) p.aux[e] = 0;
+    if (p.cn) p.cn[e] = 0.0f;
+    if (p.jac) p.jac[e] = 0.0f;
+    if (p.ovl) p.ovl[e] = 0.0f;
+    if (p.tot) p.tot[e] = 0.0f;
+}
+
+// Fixed-point MinHash estimate V = round(c / (K + c) * 2^42) * (d_u + d_v).
+// The per-vertex sums add at most 32 such values per run, so a value at or
+// above 2^58 (an edge between two vertices of ~2^16+ neighbours with
+// near-identical sketches) is not carried in fixed point: fx_ok = false and
+// the caller adds the double estimate directly.
+__device__ __forceinline__ unsigned long long minhash_fixed(unsigned long long tv, uint32_t ds, bool &fx_ok) {
+    const unsigned long long lo = tv * (unsigned long long)ds;
+    fx_ok = __umul64hi(tv, (unsigned long long)ds) == 0ull && lo < (1ull << 58);
+    return fx_ok ? lo : 0ull;
+}
+
 // Layout of a Bloom / k-Hash pass: a group of L lanes holds a sketch row as
 // L x VPL 16-byte vectors and owns B items per iteration (every L/B-th lane
 // owns one: it fetches the item, receives its reduced count and runs its
@@ -285,6 +328,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
     int32_t cu, cv, cdu, cdv;
     item<PAIRS>(p, w0 + slot, w1, p.need_deg != 0, cu, cv, cdu, cdv);
     int32_t cur_u = -1;  // UREUSE: vertex whose row slice is in cur_row
+    unsigned long long dsum = 0ull;  // OR estimator: this lane's sum of d_u + d_v
     uint4 cur_row[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) cur_row[q] = make_uint4(0u, 0u, 0u, 0u);
@@ -311,7 +355,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
                 for (int q = 0; q < VPL; ++q) {
                     const int idx = (int)g + q * L;
                     const bool in = us[t] >= 0 && idx < p.nvec;
-                    rb[t][q] = in ? ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx) : make_uint4(1u, 1u, 1u, 1u);
+                    rb[t][q] = in ? ldg4(p.data + (int64_t)vs[t] * p.stride + 16 * idx)
+                                  : (KIND == BLOOM ? make_uint4(0u, 0u, 0u, 0u) : make_uint4(1u, 1u, 1u, 1u));
                     if (reuse)
                         ra[t][q] = cur_row[q];
                     else
@@ -336,16 +381,25 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
         // ---- epilogue: the owner lane of each edge
         const int64_t e = eb + slot;
         unsigned long long V = 0ull;  // estimate * 2^42
-        if (owner && cu == -2) {  // invalid pair
-            if (p.count) p.count[e] = 0;
-            if (p.cn) p.cn[e] = 0.0f;
-            if (p.jac) p.jac[e] = 0.0f;
-        }
+        if (owner && cu == -2) write_zero(p, e);  // invalid pair
         if (owner && cu >= 0) {
             if (KIND == KHASH && (cdu == 0 || cdv == 0)) c = 0;
             float est_f = 0.0f;
             double est_d = 0.0;
-            if (KIND == BLOOM) {
+            bool fx_ok = true;
+            const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
+            if (KIND == BLOOM && p.want_union) {
+                // OR estimator: |X| + |Y| + (l/b) log(1 - U~/l), the table holding the logarithm term
+                const uint32_t U = c >> 16;
+                c &= 0xFFFFu;
+                est_d = (double)ds + tab[U];
+                est_f = (float)est_d;
+                fx_ok = est_d >= 0.0 && est_d < 65536.0;
+                V = fx_ok ? __double2ull_rn(ldexp(est_d, kFixBits)) : 0ull;
+                if (want_hist) atomicAdd(h32 + U, 1u);
+                dsum += ds;
+                if (p.aux) p.aux[e] = (int32_t)U;
+            } else if (KIND == BLOOM) {
                 if (p.need_est) {
                     V = tabV[c];
                     est_d = tab[c];
@@ -353,10 +407,9 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
                 }
                 if (want_hist) atomicAdd(h32 + c, 1u);
             } else {
-                const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
                 if (p.need_est) {
-                    V = tabV[c] * (unsigned long long)ds;
-                    est_d = p.S ? fx_to_f64(V) : 0.0;
+                    V = minhash_fixed(tabV[c], ds, fx_ok);
+                    est_d = fx_ok ? (p.S ? fx_to_f64(V) : 0.0) : tab[c] * (double)ds;
                     est_f = tabF[c] * (float)ds;
                 }
                 if (want_hist) {
@@ -366,16 +419,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
                 }
             }
             if (p.count) p.count[e] = (int32_t)c;
-            if (p.cn) p.cn[e] = est_f;
-            if (p.jac) {
-                const float fu = (float)cdu, fv = (float)cdv;
-                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
-                const float den = fu + fv - I;
-                p.jac[e] = den > 0.0f ? I / den : 0.0f;
-            }
+            write_sims(p, e, est_f, cdu, cdv);
             if (p.S) {
                 atomicAdd(p.S + cv, est_d);
-                if (PAIRS) atomicAdd(p.S + cu, est_d);
+                if (PAIRS || !fx_ok) atomicAdd(p.S + cu, est_d);
             }
         }
         // non-owner lanes carry their owner's u (cu) with a zero value, so runs stay contiguous
@@ -387,6 +434,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
     }
 
     if (want_hist) {
+        if (KIND == BLOOM && p.want_union) {
+            // OR estimator: the exact sum of d_u + d_v goes to the bin after the l + 1 union counts
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+            if (lane == 0 && dsum) atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + p.l + 1), dsum);
+        }
         __syncthreads();
         if (KIND == BLOOM) {
             for (int i = threadIdx.x; i < h32_len; i += blockDim.x)
@@ -531,8 +584,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             } else {
                 const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
                 if (p.need_est) {
-                    V = tabV[c] * (unsigned long long)ds;
-                    est_d = p.S ? fx_to_f64(V) : 0.0;
+                    bool fx_ok;
+                    V = minhash_fixed(tabV[c], ds, fx_ok);
+                    est_d = fx_ok ? (p.S ? fx_to_f64(V) : 0.0) : tab[c] * (double)ds;
+                    if (!fx_ok && p.S) atomicAdd(p.S + cu, est_d);  // too large for the fixed-point run sum
                     est_f = tabF[c] * (float)ds;
                 }
                 if (want_hist) {
@@ -542,13 +597,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
                 }
             }
             if (p.count) p.count[e] = (int32_t)c;
-            if (p.cn) p.cn[e] = est_f;
-            if (p.jac) {
-                const float fu = (float)cdu, fv = (float)cdv;
-                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
-                const float den = fu + fv - I;
-                p.jac[e] = den > 0.0f ? I / den : 0.0f;
-            }
+            write_sims(p, e, est_f, cdu, cdv);
             if (p.S) atomicAdd(p.S + cv, est_d);
         }
         if (p.S) add_u_runs(p.S, cu, V);
@@ -654,16 +703,13 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
         }
         // ---- epilogue: lane t owns edge t
         const int64_t e = eb + lane;
-        if (lane < (unsigned)kB && cu == -2) {
-            if (p.count) p.count[e] = 0;
-            if (p.aux) p.aux[e] = 0;
-            if (p.cn) p.cn[e] = 0.0f;
-            if (p.jac) p.jac[e] = 0.0f;
-        }
+        if (lane < (unsigned)kB && cu == -2) write_zero(p, e);
         if (lane < (unsigned)kB && cu >= 0) {
             const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
             const int ti = (p.est == PG_EST_1H_LITERAL) ? (int)k * hk + lit_u : K_u * hk + cnt_u;
-            const unsigned long long V = tabV[ti] * (unsigned long long)ds;
+            bool fx_ok;
+            const unsigned long long V = minhash_fixed(tabV[ti], ds, fx_ok);
+            const double big = fx_ok ? 0.0 : tab[ti] * (double)ds;
             const float est_f = tabF[ti] * (float)ds;
             if (want_hist) {
                 const int bin = K_u * hk + cnt_u;
@@ -676,14 +722,11 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
             }
             if (p.aux) p.aux[e] = K_u | (lit_u << 16);
             if (p.count) p.count[e] = (p.est == PG_EST_1H_LITERAL) ? lit_u : cnt_u;
-            if (p.cn) p.cn[e] = est_f;
-            if (p.jac) {
-                const float fu = (float)cdu, fv = (float)cdv;
-                const float I = fminf(fmaxf(est_f, 0.0f), fminf(fu, fv));
-                const float den = fu + fv - I;
-                p.jac[e] = den > 0.0f ? I / den : 0.0f;
-            }
-            if (p.S) {
+            write_sims(p, e, est_f, cdu, cdv);
+            if (p.S && !fx_ok) {  // too large for fixed point: double atomics on both sides
+                atomicAdd(p.S + cv, big);
+                atomicAdd(p.S + cu, big);
+            } else if (p.S) {
                 atomicAdd(p.S + cv, fx_to_f64(V));
                 if (PAIRS) {
                     atomicAdd(p.S + cu, fx_to_f64(V));
@@ -691,6 +734,10 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
                     if (cu != acc_vertex) {
                         if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
                         acc_vertex = cu;
+                        acc_u = 0ull;
+                    }
+                    if (acc_u >= (1ull << 62)) {  // keep the running sum below 2^62 + 2^58
+                        atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
                         acc_u = 0ull;
                     }
                     acc_u += V;
@@ -731,10 +778,14 @@ __global__ void k_table(double *tab, int32_t len, int32_t kind, int32_t est, uin
         double v;
         if (kind == BLOOM) {
             const uint32_t j = (uint32_t)i;
+            const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
             if (est == PG_EST_BF_L) {
                 v = (double)j / (double)b;
+            } else if (est == PG_EST_BF_OR) {  // indexed by the union count; the caller adds d_u + d_v
+                v = ((double)l / (double)b) * log(1.0 - B1 / (double)l);
+            } else if (est == PG_EST_BF_SS) {
+                v = log(1.0 - B1 / (double)l) / ((double)b * log(1.0 - 1.0 / (double)l));
             } else {
-                const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
                 v = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
             }
         } else {
@@ -758,13 +809,24 @@ __device__ __forceinline__ void tc_dot_block(const uint64_t *__restrict__ hist, 
     double main_ = 0.0, alt = 0.0;
     unsigned long long edges = 0, sum = 0;
     const uint32_t hk = k + 1;
-    if (kind == BLOOM) {
+    if (kind == BLOOM && est == PG_EST_BF_OR) {
+        // bins 0..l: union counts; bin l + 1: the exact sum of d_u + d_v
+        for (uint32_t j = threadIdx.x; j <= l; j += blockDim.x) {
+            const unsigned long long h = hist[j];
+            const double U = (j == l) ? (double)j - 1.0 : (double)j;
+            main_ += (double)h * (((double)l / (double)b) * log(1.0 - U / (double)l));
+            edges += h;
+            sum += h * j;
+        }
+        if (threadIdx.x == 0) main_ += (double)hist[l + 1];
+    } else if (kind == BLOOM) {
         for (uint32_t j = threadIdx.x; j <= l; j += blockDim.x) {
             const unsigned long long h = hist[j];
             const double B1 = (j == l) ? (double)j - 1.0 : (double)j;
             const double f_and = -((double)l / (double)b) * log(1.0 - B1 / (double)l);
             const double f_l = (double)j / (double)b;
-            main_ += (double)h * (est == PG_EST_BF_L ? f_l : f_and);
+            const double f_ss = log(1.0 - B1 / (double)l) / ((double)b * log(1.0 - 1.0 / (double)l));
+            main_ += (double)h * (est == PG_EST_BF_L ? f_l : est == PG_EST_BF_SS ? f_ss : f_and);
             alt += (double)h * (est == PG_EST_BF_L ? f_and : f_l);
             edges += h;
             sum += h * j;
@@ -901,8 +963,8 @@ int pow2_at_least(int x) {
 
 }  // namespace
 
-int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k) {
-    if (kind == BLOOM) return (int64_t)l + 1;
+int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k, int32_t estimator) {
+    if (kind == BLOOM) return (int64_t)l + 1 + (estimator == PG_EST_BF_OR ? 1 : 0);
     if (kind == KHASH) return 2 * ((int64_t)k + 1);
     if (kind == ONEHASH) return 2 * ((int64_t)k + 1) * (k + 1) + 2 * ((int64_t)k + 1);
     return 0;
@@ -944,20 +1006,25 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     p.S = out.S;
     p.cn = out.cn;
     p.jac = out.jac;
+    p.ovl = out.ovl;
+    p.tot = out.tot;
     p.count = out.count;
     p.aux = out.aux;
     p.hist = out.hist;
-    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k);
+    p.want_union = (sk.kind == PG_SK_BLOOM && estimator == PG_EST_BF_OR) ? 1 : 0;
+    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k, estimator);
     p.table = table_ws;
     p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
-    p.need_est = (out.S || out.cn || out.jac) ? 1 : 0;
-    p.need_deg = (sk.kind != PG_SK_BLOOM || out.jac) ? 1 : 0;
+    const bool sims = out.jac || out.ovl || out.tot;
+    p.need_est = (out.S || out.cn || sims) ? 1 : 0;
+    p.need_deg = (sk.kind != PG_SK_BLOOM || sims || p.want_union) ? 1 : 0;
     k_table<<<1, 256, 0, s>>>(table_ws, p.table_len, sk.kind, estimator, sk.bits, sk.b, sk.k);
     note_launch();
     const bool pr = pairs != nullptr;
     if (pr && P == 0) return cudaGetLastError();
+    // the OR estimator counts two popcounts per word: generic pass kernels only
 #define PG_LEAN(KIND, L, W, SB, UR, MB) \
-    if (!pr) return run_lean<KIND, L, W, SB, UR, MB>(p, s)
+    if (!pr && !p.want_union) return run_lean<KIND, L, W, SB, UR, MB>(p, s)
 #define PG_PASS(KIND, L, VPL, B, SB, UR, MB) \
     return pr ? run_pass<KIND, L, VPL, B, SB, UR, MB, true>(p, s) : run_pass<KIND, L, VPL, B, SB, UR, MB, false>(p, s)
     if (sk.kind == PG_SK_BLOOM) {
@@ -1024,7 +1091,7 @@ cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_
     p.est = estimator;
     p.S = S;
     p.hist = hist;
-    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k);
+    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k, estimator);
     p.table = table_ws;
     p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
     p.need_est = S ? 1 : 0;

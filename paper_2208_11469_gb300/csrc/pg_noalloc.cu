@@ -81,7 +81,7 @@ extern "C" pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *inde
     PG_REQUIRE(out != nullptr && (reinterpret_cast<uintptr_t>(out) & 7u) == 0, PG_ERR_INVALID_ARG,
                "pg_triangle_count_noalloc: out must be an 8-byte aligned device pg_tc_result");
     const size_t table = intersect_table_bytes(sk->kind, sk->bits, sk->k);
-    const size_t bins = (size_t)hist_bins(sk->kind, sk->bits, sk->k);
+    const size_t bins = (size_t)hist_bins(sk->kind, sk->bits, sk->k, estimator);
     const size_t scratch = table + 8 * bins;
     PG_REQUIRE(scratch <= kNoallocScratchBytes, PG_ERR_TOO_LARGE,
                "pg_triangle_count_noalloc: this sketch needs %zu bytes of scratch, the static "

@@ -24,6 +24,7 @@ ERR = {0: "PG_OK", -1: "PG_ERR_INVALID_ARG", -2: "PG_ERR_INVALID_GRAPH", -3: "PG
        -8: "PG_ERR_BUSY", -9: "PG_ERR_UNSUPPORTED", -10: "PG_ERR_CANCELLED"}
 SK_BLOOM, SK_KHASH, SK_1HASH = 1, 2, 3
 EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
+EST_BF_OR, EST_BF_SS = 6, 7
 CSR_CODES = {0: "ok", 1: "bad_row_ptr", 2: "out_of_range", 3: "unsorted", 4: "self_loop", 5: "asymmetric"}
 
 # Every symbol include/pg.h declares.
@@ -32,7 +33,7 @@ SYMBOLS = [
     "pg_build_edge_index", "pg_edge_index_upper_off", "pg_sketch_stride",
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
-    "pg_jaccard_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
+    "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
     "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_submit_many", "pg_poll_many", "pg_poll",
@@ -61,7 +62,13 @@ class SketchDesc(ctypes.Structure):
 class Outputs(ctypes.Structure):
     _fields_ = [("tc", ctypes.c_void_p), ("lcc", ctypes.c_void_p), ("tri", ctypes.c_void_p),
                 ("edge_cn", ctypes.c_void_p), ("edge_jac", ctypes.c_void_p), ("edge_count", ctypes.c_void_p),
-                ("edge_aux", ctypes.c_void_p), ("hist", ctypes.c_void_p)]
+                ("edge_aux", ctypes.c_void_p), ("hist", ctypes.c_void_p), ("edge_overlap", ctypes.c_void_p),
+                ("edge_total", ctypes.c_void_p)]
+
+
+class Similarity(ctypes.Structure):
+    _fields_ = [("cn", ctypes.c_void_p), ("jac", ctypes.c_void_p), ("overlap", ctypes.c_void_p),
+                ("total", ctypes.c_void_p)]
 
 
 class BatchConfig(ctypes.Structure):
@@ -148,6 +155,7 @@ def lib() -> ctypes.CDLL:
                 "pg_triangle_count": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, vp, vp]),
                 "pg_clustering": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, vp, vp, vp, vp]),
                 "pg_jaccard_pairs": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, vp, vp, vp]),
+                "pg_similarity_pairs": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, P(Similarity), vp]),
                 "pg_edge_counts": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, i64, vp, sz, vp, vp, vp, vp]),
                 "pg_kernel_launches": (ctypes.c_uint64, []),
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
@@ -420,6 +428,23 @@ def jaccard_pairs(g: Graph, sk: Sketch | None, est: int, pairs: torch.Tensor | N
     return cn, jac
 
 
+def similarity_pairs(g: Graph, sk: Sketch | None, est: int, pairs: torch.Tensor | None = None, *,
+                     ws: torch.Tensor | None = None):
+    """pg_similarity_pairs: dict of float32 tensors cn, jac, overlap, total
+    (per pair, or per upper edge with pairs None)."""
+    pairs, P = _pairs_arg(pairs)
+    count = P if pairs is not None else g.m
+    ws = ws if ws is not None else workspace(g, sk, est)
+    out = {nm: torch.empty(max(count, 1), dtype=torch.float32, device=g.device)
+           for nm in ("cn", "jac", "overlap", "total")}
+    sim = Similarity(*[out[nm].data_ptr() for nm in ("cn", "jac", "overlap", "total")])
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_similarity_pairs(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(pairs), P, _ptr(ws),
+                                     ws.numel(), ctypes.byref(sim), _stream()), "pg_similarity_pairs")
+    return {nm: t[:count] for nm, t in out.items()}
+
+
 def edge_counts(g: Graph, sk: Sketch | None, est: int, pairs: torch.Tensor | None = None, *,
                 want_aux: bool = False, want_hist: bool = False, ws: torch.Tensor | None = None):
     pairs, P = _pairs_arg(pairs)
@@ -440,12 +465,14 @@ def kernel_launches() -> int:
 
 
 def analyze(g: Graph, sk: Sketch | None, est: int, *, tc=None, lcc=None, tri=None, edge_cn=None,
-            edge_jac=None, edge_count=None, edge_aux=None, hist=None, ws: torch.Tensor | None = None):
+            edge_jac=None, edge_count=None, edge_aux=None, hist=None, edge_overlap=None, edge_total=None,
+            ws: torch.Tensor | None = None):
     """One fused pass (pg_analyze). Pass preallocated device tensors for the
     outputs wanted; None leaves an output out."""
     ws = ws if ws is not None else workspace(g, sk, est)
     o = Outputs(*[t.data_ptr() if t is not None else None
-                  for t in (tc, lcc, tri, edge_cn, edge_jac, edge_count, edge_aux, hist)])
+                  for t in (tc, lcc, tri, edge_cn, edge_jac, edge_count, edge_aux, hist, edge_overlap,
+                            edge_total)])
     c = g.csr()
     d, dref = _sk_args(sk)
     _check(lib().pg_analyze(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(ws), ws.numel(), ctypes.byref(o),
