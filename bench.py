@@ -1,7 +1,7 @@
 """Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload rmat24|rmat24_b50|rmat22|rmat20|er4096|batch4096|serve22|jp22]
+                    [--workload rmat24|rmat24_b50|rmat22|rmat20|variants20|er4096|batch4096|serve22|jp22]
                     [--impl ours|reference]
 
 A step is one pass of the whole sketched path over the synthetic graph of the
@@ -49,6 +49,10 @@ WORKLOADS = {
     "rmat22": dict(gen=("rmat", 22, 32, 22), budget=0.25, b=2, khash=64, onehash=None, jaccard=False),
     # R-MAT scale 20, edge factor 16, Bloom at 25% (b = 2), 1-Hash k = 32, TC + LCC + per-edge Jaccard
     "rmat20": dict(gen=("rmat", 20, 16, 20), budget=0.25, b=2, khash=None, onehash=32, jaccard=True),
+    # the estimator variants on R-MAT scale 20 / edge factor 16: Bloom at 25% (b = 2) read by AND, OR and
+    # the single-set form, with per-edge Jaccard, overlap and total-neighbour similarities
+    "variants20": dict(gen=("rmat", 20, 16, 20), budget=0.25, b=2, khash=None, onehash=None, jaccard=True,
+                       similarity=True, bloom_variants=("or", "ss")),
     # Erdos-Renyi n = 4096, average degree 16, Bloom 256 bits b = 2, k-Hash k = 16
     "er4096": dict(gen=("er", 4096, 16.0, 1), bits=256, b=2, khash=16, onehash=None, jaccard=False),
     # 4096 graphs (half Erdos-Renyi, half R-MAT), n log-uniform in [2^8, 2^16], average degree
@@ -217,9 +221,12 @@ class Pipeline:
         bits = cfg.get("bits") or pg.bloom_bits_for_budget(cfg["budget"], g.n, g.nnz)
         self.bits = bits
         self.build_ws = torch.empty(max(pg.build_workspace_bytes(g), 16), dtype=torch.uint8, device=dev)
-        self.passes = []  # (name, sketch, estimator, build_fn)
+        self.passes = []  # (name, sketch, estimator)
         bf = pg.alloc_sketch(g, pg.SK_BLOOM, bits=bits, b=cfg["b"], seed=1)
         self.passes.append(("bloom", bf, pg.EST_BF_AND))
+        # further estimators on the same Bloom sketch (built once per step)
+        for nm in cfg.get("bloom_variants", ()):
+            self.passes.append(("bloom_" + nm, bf, {"or": pg.EST_BF_OR, "ss": pg.EST_BF_SS, "l": pg.EST_BF_L}[nm]))
         if cfg["khash"]:
             self.passes.append(("khash", pg.alloc_sketch(g, pg.SK_KHASH, k=cfg["khash"], seed=1), pg.EST_KH))
         if cfg["onehash"]:
@@ -232,6 +239,9 @@ class Pipeline:
             if cfg["jaccard"]:
                 o["edge_cn"] = torch.empty(self.m, dtype=torch.float32, device=dev)
                 o["edge_jac"] = torch.empty(self.m, dtype=torch.float32, device=dev)
+            if cfg.get("similarity"):
+                o["edge_overlap"] = torch.empty(self.m, dtype=torch.float32, device=dev)
+                o["edge_total"] = torch.empty(self.m, dtype=torch.float32, device=dev)
             self.out[name] = o
         self.index_events = None
 
@@ -250,7 +260,11 @@ class Pipeline:
         mark("index", 0)
         pg.build_edge_index_into(g)
         mark("index", 1)
+        built = set()
         for name, sk, est in self.passes:
+            if id(sk) in built:
+                continue
+            built.add(id(sk))
             mark("build_" + name, 0)
             if sk.kind == pg.SK_BLOOM:
                 pg.build_bloom(g, sk.bits, sk.b, sk.seed, out=sk, workspace=self.build_ws)
@@ -263,7 +277,12 @@ class Pipeline:
             mark("pass_" + name, 1)
 
     def event_names(self):
-        return ["index"] + ["build_" + p[0] for p in self.passes] + ["pass_" + p[0] for p in self.passes]
+        builds, seen = [], set()
+        for name, sk, _ in self.passes:
+            if id(sk) not in seen:
+                seen.add(id(sk))
+                builds.append("build_" + name)
+        return ["index"] + builds + ["pass_" + p[0] for p in self.passes]
 
     def results(self):
         return {name: self.pg.read_tc_result(self.out[name]["tc"]) for name, _, _ in self.passes}
@@ -276,10 +295,13 @@ def algorithmic_bytes(pipe: Pipeline, name: str) -> float:
     its own sketch row, its two row offsets and upper offset, and the outputs
     (T as double, LCC as float)."""
     sk = [p for p in pipe.passes if p[0] == name][0][1]
+    est = [p for p in pipe.passes if p[0] == name][0][2]
     payload = sk.bits / 8 if sk.kind == pipe.pg.SK_BLOOM else 4 * sk.k
-    per_edge = payload + 4 + (8 if sk.kind != pipe.pg.SK_BLOOM else 0)
+    per_edge = payload + 4 + (8 if sk.kind != pipe.pg.SK_BLOOM or est == pipe.pg.EST_BF_OR else 0)
     per_vertex = payload + 8 + 4 + 8 + 4
     if pipe.cfg["jaccard"]:
+        per_edge += 8
+    if pipe.cfg.get("similarity"):
         per_edge += 8
     return pipe.m * per_edge + pipe.n * per_vertex
 
