@@ -9,8 +9,9 @@
 //     popcount(B_u AND B_v) or equal minima lane-wise and reduce-scatters the
 //     counts so that each edge ends on its owner lane, which runs the
 //     epilogue (estimate, histogram, per-vertex sums, outputs).
-//   1-Hash (k_onehash): one warp per edge, lane r holds entry r of each row;
-//     the counts come from a warp-wide merge (reading C of the design notes).
+//   1-Hash (k_onehash): one lane per edge merges its two bottom-k rows,
+//     staged in shared memory, into c_union among the K smallest values of
+//     the union (and the literal common count when asked for).
 // Graph totals come from exact integer histograms of the counts (block-local
 // in shared memory with 32-bit atomics, merged with 64-bit integer atomics)
 // and one fixed-order double dot product in k_tc_finalize, so they are
@@ -23,7 +24,6 @@ namespace pg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 __host__ __device__ __forceinline__ int32_t round_up4(int32_t x) { return (x + 3) & ~3; }
 
@@ -114,35 +114,6 @@ __device__ __forceinline__ uint32_t lane_count(const Params &p, const uint4 (&a)
         }
     }
     return c;
-}
-
-// 1-Hash counts for one edge, whole warp (lane r holds entry r of each row).
-__device__ __forceinline__ void onehash_counts(uint32_t su, uint32_t sv, int la, int lb, int k,
-                                               int &c_union, int &K, int &c_lit) {
-    const unsigned r = lane_id();
-    const uint32_t x = su;
-    int pos = 0;
-#pragma unroll
-    for (int step = 16; step >= 1; step >>= 1) {
-        const int probe = pos + step - 1;
-        const uint32_t pv = __shfl_sync(0xffffffffu, sv, probe);
-        if (probe < lb && pv < x) pos += step;
-    }
-    const uint32_t pv = __shfl_sync(0xffffffffu, sv, pos & 31);
-    bool found = false;
-    if (pos < lb) {
-        if (pv < x)
-            ++pos;
-        else
-            found = (pv == x);
-    }
-    found = found && ((int)r < la);
-    const unsigned fm = __ballot_sync(0xffffffffu, found);
-    c_lit = __popc(fm);
-    const int U = la + lb - c_lit;
-    K = U < k ? U : k;
-    const int rank = (int)r + pos - __popc(fm & ((1u << r) - 1u));
-    c_union = __popc(__ballot_sync(0xffffffffu, found && rank < K));
 }
 
 // ---------------------------------------------------------------------------
@@ -632,11 +603,22 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
 }
 
 // ---------------------------------------------------------------------------
-// 1-Hash pass: one warp per edge, kB edges per iteration (lane t < kB fetches
-// and owns edge t of the iteration).
+// 1-Hash pass: one lane per edge (32 edges per warp iteration). Each lane
+// copies its two bottom-k rows into the warp's shared staging area, stored
+// transposed (entry i of lane r's row at [i * 32 + r]) so that a lane only
+// ever touches its own bank, then merges them itself (reading C):
+//   phase 1 - the K = min(k, |S_u ∪ S_v|) smallest distinct values, counting
+//             the c_union values present in both rows;
+//   phase 2 - (only when the literal count is needed) the rest of the merge,
+//             counting the common values of the two whole rows (c_lit).
+// A merge step takes the smaller head (both on a tie); rows hold distinct
+// values, so each step emits one distinct value of the union. The loops stop
+// when no lane of the warp has entries left. Histogram updates are
+// aggregated over the lanes with the same bin (one shared atomic per bin).
+constexpr int kOneHashWarps = kThreads / 32;
+
 template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
-    constexpr int kB = 4;
     extern __shared__ __align__(16) unsigned char smem[];
     double *tab = reinterpret_cast<double *>(smem);
     unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
@@ -648,6 +630,11 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
     // literal counts [k+1], literal degree-sum low words and carries [k+1] each
     const int h32_len = 3 * hk2 + 3 * hk;
     const bool want_hist = p.hist != nullptr;
+    const bool want_lit = want_hist || p.aux != nullptr || p.est == PG_EST_1H_LITERAL;
+    uint32_t *stage = h32 + (want_hist ? round_up4(h32_len) : 0);
+    const unsigned lane = lane_id();
+    uint32_t *A = stage + (size_t)(threadIdx.x >> 5) * 2 * (k + 1) * 32 + lane;
+    uint32_t *Bv = A + (size_t)(k + 1) * 32;
     {
         const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
         const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
@@ -661,95 +648,103 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
     __syncthreads();
 
-    const unsigned lane = lane_id();
+    const int nv4 = (int)((k + 3) / 4);
     int64_t w0, w1;
     warp_range<PAIRS>(p, w0, w1);
-    const int32_t iters = (int32_t)((w1 - w0 + kB - 1) / kB);
-    int32_t cu = -1, cv = -1, cdu = 0, cdv = 0;
-    if (lane < (unsigned)kB) item<PAIRS>(p, w0 + lane, w1, true, cu, cv, cdu, cdv);
-    unsigned long long acc_u = 0ull;  // fixed-point sum for acc_vertex
-    int32_t acc_vertex = -1;
+    const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
     for (int32_t it = 0; it < iters; ++it) {
-        const int64_t eb = w0 + (int64_t)it * kB;
-        int32_t us[kB], vs[kB], dus[kB], dvs[kB];
-        uint32_t su[kB], sv[kB];
-#pragma unroll
-        for (int t = 0; t < kB; ++t) {
-            us[t] = __shfl_sync(0xffffffffu, cu, t);
-            vs[t] = __shfl_sync(0xffffffffu, cv, t);
-            dus[t] = __shfl_sync(0xffffffffu, cdu, t);
-            dvs[t] = __shfl_sync(0xffffffffu, cdv, t);
-        }
-#pragma unroll
-        for (int t = 0; t < kB; ++t) {
-            su[t] = sv[t] = kEmpty;
-            if (us[t] >= 0 && lane < k) {
-                su[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)us[t] * p.stride) + lane);
-                sv[t] = __ldg(reinterpret_cast<const uint32_t *>(p.data + (int64_t)vs[t] * p.stride) + lane);
+        const int64_t e = w0 + (int64_t)it * 32 + lane;
+        int32_t cu, cv, cdu, cdv;
+        item<PAIRS>(p, e, w1, true, cu, cv, cdu, cdv);
+        const bool valid = cu >= 0;
+        const uint32_t la = valid ? min(k, (uint32_t)cdu) : 0u, lb = valid ? min(k, (uint32_t)cdv) : 0u;
+        // stage the two rows (whole 16-byte vectors; entries past min(k, d) are never read)
+        if (valid) {
+            const uint4 *ru = reinterpret_cast<const uint4 *>(p.data + (int64_t)cu * p.stride);
+            const uint4 *rv = reinterpret_cast<const uint4 *>(p.data + (int64_t)cv * p.stride);
+            for (int q = 0; q < nv4; ++q) {
+                const uint4 x = __ldg(ru + q), y = __ldg(rv + q);
+                A[(4 * q + 0) * 32] = x.x;
+                A[(4 * q + 1) * 32] = x.y;
+                A[(4 * q + 2) * 32] = x.z;
+                A[(4 * q + 3) * 32] = x.w;
+                Bv[(4 * q + 0) * 32] = y.x;
+                Bv[(4 * q + 1) * 32] = y.y;
+                Bv[(4 * q + 2) * 32] = y.z;
+                Bv[(4 * q + 3) * 32] = y.w;
             }
         }
-        int32_t nu = -1, nv = -1, ndu = 0, ndv = 0;
-        if (lane < (unsigned)kB) item<PAIRS>(p, eb + kB + lane, w1, true, nu, nv, ndu, ndv);
-        int cnt_u = 0, K_u = 0, lit_u = 0;
-#pragma unroll
-        for (int t = 0; t < kB; ++t) {
-            int cu_, K_, lit_;
-            onehash_counts(su[t], sv[t], min((int)k, dus[t]), min((int)k, dvs[t]), (int)k, cu_, K_, lit_);
-            if ((int)lane == t) {
-                cnt_u = cu_;
-                K_u = K_;
-                lit_u = lit_;
+        __syncwarp();
+        // phase 1: the K smallest distinct values of the union
+        uint32_t i = 0, j = 0, K = 0, cun = 0;
+        for (uint32_t st = 0; st < k; ++st) {
+            const bool ha = i < la, hb = j < lb;
+            if (!__any_sync(0xffffffffu, ha || hb)) break;
+            const uint32_t x = A[i * 32], y = Bv[j * 32];
+            const bool ta = ha && (!hb || x <= y);
+            const bool tb = hb && (!ha || y <= x);
+            K += (ha || hb);
+            cun += (ta && tb);
+            i += ta;
+            j += tb;
+        }
+        // phase 2: common values among the rest of the two rows
+        uint32_t clit = cun;
+        if (want_lit) {
+            for (uint32_t st = 0; st < 2 * k; ++st) {
+                const bool ha = i < la, hb = j < lb;
+                if (!__any_sync(0xffffffffu, ha && hb)) break;
+                const uint32_t x = A[i * 32], y = Bv[j * 32];
+                const bool both = ha && hb;
+                clit += (both && x == y);
+                i += both && x <= y;
+                j += both && y <= x;
             }
         }
-        // ---- epilogue: lane t owns edge t
-        const int64_t e = eb + lane;
-        if (lane < (unsigned)kB && cu == -2) write_zero(p, e);
-        if (lane < (unsigned)kB && cu >= 0) {
-            const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
-            const int ti = (p.est == PG_EST_1H_LITERAL) ? (int)k * hk + lit_u : K_u * hk + cnt_u;
-            bool fx_ok;
-            const unsigned long long V = minhash_fixed(tabV[ti], ds, fx_ok);
-            const double big = fx_ok ? 0.0 : tab[ti] * (double)ds;
+        __syncwarp();  // the staging area is rewritten by the next iteration
+
+        // ---- epilogue: every lane for its own edge
+        unsigned long long V = 0ull;
+        bool fx_ok = true;
+        double big = 0.0;
+        uint32_t ds = 0;
+        if (cu == -2) write_zero(p, e);
+        if (valid) {
+            ds = (uint32_t)cdu + (uint32_t)cdv;
+            const int ti = (p.est == PG_EST_1H_LITERAL) ? (int)k * hk + (int)clit : (int)K * hk + (int)cun;
+            V = minhash_fixed(tabV[ti], ds, fx_ok);
+            if (!fx_ok) big = tab[ti] * (double)ds;
             const float est_f = tabF[ti] * (float)ds;
-            if (want_hist) {
-                const int bin = K_u * hk + cnt_u;
-                atomicAdd(h32 + bin, 1u);
-                uint32_t old = atomicAdd(h32 + hk2 + bin, ds);
-                if (old + ds < old) atomicAdd(h32 + 2 * hk2 + bin, 1u);
-                atomicAdd(h32 + 3 * hk2 + lit_u, 1u);
-                old = atomicAdd(h32 + 3 * hk2 + hk + lit_u, ds);
-                if (old + ds < old) atomicAdd(h32 + 3 * hk2 + 2 * hk + lit_u, 1u);
-            }
-            if (p.aux) p.aux[e] = K_u | (lit_u << 16);
-            if (p.count) p.count[e] = (p.est == PG_EST_1H_LITERAL) ? lit_u : cnt_u;
+            if (p.aux) p.aux[e] = (int32_t)(K | (clit << 16));
+            if (p.count) p.count[e] = (int32_t)((p.est == PG_EST_1H_LITERAL) ? clit : cun);
             write_sims(p, e, est_f, cdu, cdv);
-            if (p.S && !fx_ok) {  // too large for fixed point: double atomics on both sides
-                atomicAdd(p.S + cv, big);
-                atomicAdd(p.S + cu, big);
-            } else if (p.S) {
-                atomicAdd(p.S + cv, fx_to_f64(V));
-                if (PAIRS) {
-                    atomicAdd(p.S + cu, fx_to_f64(V));
-                } else {
-                    if (cu != acc_vertex) {
-                        if (acc_vertex >= 0) atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
-                        acc_vertex = cu;
-                        acc_u = 0ull;
-                    }
-                    if (acc_u >= (1ull << 62)) {  // keep the running sum below 2^62 + 2^58
-                        atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
-                        acc_u = 0ull;
-                    }
-                    acc_u += V;
-                }
+            if (p.S) {
+                const double est_d = fx_ok ? fx_to_f64(V) : big;
+                atomicAdd(p.S + cv, est_d);
+                if (PAIRS || !fx_ok) atomicAdd(p.S + cu, est_d);
             }
         }
-        cu = nu;
-        cv = nv;
-        cdu = ndu;
-        cdv = ndv;
+        if (!PAIRS && p.S) add_u_runs(p.S, cu, fx_ok ? V : 0ull);
+        if (want_hist) {
+            // lanes with the same bin add together: one shared atomic per distinct bin
+            const uint32_t bin = valid ? K * (uint32_t)hk + cun : 0xFFFFFFFFu;
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            const uint32_t dsum = __reduce_add_sync(same, ds);
+            if (valid && (int)lane == __ffs(same) - 1) {
+                atomicAdd(h32 + bin, (uint32_t)__popc(same));
+                const uint32_t old = atomicAdd(h32 + hk2 + bin, dsum);
+                if (old + dsum < old) atomicAdd(h32 + 2 * hk2 + bin, 1u);
+            }
+            const uint32_t lbin = valid ? clit : 0xFFFFFFFFu;
+            const unsigned lsame = __match_any_sync(0xffffffffu, lbin);
+            const uint32_t ldsum = __reduce_add_sync(lsame, ds);
+            if (valid && (int)lane == __ffs(lsame) - 1) {
+                atomicAdd(h32 + 3 * hk2 + lbin, (uint32_t)__popc(lsame));
+                const uint32_t old = atomicAdd(h32 + 3 * hk2 + hk + lbin, ldsum);
+                if (old + ldsum < old) atomicAdd(h32 + 3 * hk2 + 2 * hk + lbin, 1u);
+            }
+        }
     }
-    if (!PAIRS && p.S && acc_vertex >= 0) atomicAdd(p.S + acc_vertex, fx_to_f64(acc_u));
 
     if (want_hist) {
         __syncthreads();
@@ -904,7 +899,10 @@ __global__ void k_lcc(const int32_t *__restrict__ row_ptr, int32_t n, double *S,
 template <bool PAIRS>
 cudaError_t run_onehash(const Params &p, cudaStream_t s) {
     const int hk = (int)p.k + 1;
-    const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)(3 * hk * hk + 3 * hk) : 0);
+    // tables | histogram | per warp two staged rows of k + 1 entries x 32 lanes
+    const size_t smem = 20 * (size_t)round_up4(p.table_len) +
+                        (p.hist ? 4 * (size_t)round_up4(3 * hk * hk + 3 * hk) : 0) +
+                        4 * (size_t)kOneHashWarps * 2 * (p.k + 1) * 32;
     auto kern = k_onehash<PAIRS>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
