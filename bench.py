@@ -1,7 +1,8 @@
 """Benchmark of the sketched |N(u) ∩ N(v)| hot path on one GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W]
-                    [--workload rmat24|rmat24_b50|rmat22|rmat20|variants20|er4096|batch4096|serve22|jp22]
+                    [--workload rmat24|rmat24_b50|rmat22|rmat20|variants20|er4096|batch4096|serve22|jp22|
+                                clique20]
                     [--impl ours|reference]
 
 A step is one pass of the whole sketched path over the synthetic graph of the
@@ -65,6 +66,9 @@ WORKLOADS = {
     # Jarvis-Patrick clustering on R-MAT scale 22, edge factor 16: Bloom at 25% (b = 2) and k-Hash k = 32,
     # threshold tau = 4 common neighbours; exact clustering as the comparison
     "jp22": dict(jp=True, gen=("rmat", 22, 16, 22), budget=0.25, b=2, khash=32, tau=4.0),
+    # 4-clique counting on R-MAT scale 20, edge factor 16: Bloom filters of the oriented neighbourhoods at
+    # 256 bits, b = 2; exact 4-clique count as the comparison
+    "clique20": dict(clique=True, gen=("rmat", 20, 16, 20), bits=256, b=2),
     "serve22": dict(serve=True, gen=("rmat", 22, 16, 22), bits=512, b=2, khash=32, pair_requests=2000,
                     subgraph_requests=12, subgraph_share=0.02),
 }
@@ -100,7 +104,7 @@ def generate(workload: str, device):
     from paper_2208_11469_gb300 import synth
     if "batch" in WORKLOADS[workload]:
         return generate_batch(workload, device)
-    if "serve" in WORKLOADS[workload] or "jp" in WORKLOADS[workload]:
+    if any(k in WORKLOADS[workload] for k in ("serve", "jp", "clique")):
         kind, scale, ef, seed = WORKLOADS[workload]["gen"]
         return synth.rmat(scale, ef, seed=seed, device=device)
     kind, *a = WORKLOADS[workload]["gen"]
@@ -749,6 +753,88 @@ def run_jp(args, ws, rank, dev):
         print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- 4-cliques
+def run_clique(args, ws, rank, dev):
+    """4-clique counting: one step = orientation, Bloom filters of the oriented
+    neighbourhoods and the 3-clique enumeration with the triple-AND estimate.
+    The unit is one sketched (triple) intersection per 3-clique."""
+    from paper_2208_11469_gb300 import pg
+    w = WORKLOADS[args.workload]
+    rp, cl = generate(args.workload, dev)
+    g = pg.graph(rp, cl, build_index=False)
+    c = g.csr()
+    wsb = torch.empty(pg.lib().pg_clique4_workspace_bytes(ctypes.byref(c), pg.EST_BF_AND, w["bits"]),
+                      dtype=torch.uint8, device=dev)
+    out = torch.zeros(48, dtype=torch.uint8, device=dev)
+
+    def step():
+        pg.clique4_count(g, pg.EST_BF_AND, w["bits"], w["b"], 1, ws=wsb, out=out, read=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = pg.kernel_launches()
+    a, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index or 0) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.steps):
+            step()
+        b_.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = pg.kernel_launches() - l0
+    ms = max_over_ranks(a.elapsed_time(b_) / args.steps, ws, dev)
+    tri, _, cs, _, est, est_alt = struct.unpack("<QQQQdd", bytes(out.cpu().numpy().tobytes()))
+    exact = None
+    if not args.no_exact:
+        wse = torch.empty(pg.lib().pg_clique4_workspace_bytes(ctypes.byref(c), pg.EST_EXACT, 0),
+                          dtype=torch.uint8, device=dev)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        r = pg.clique4_count(g, pg.EST_EXACT, ws=wse)
+        eb.record()
+        torch.cuda.synchronize()
+        exact = {"ms": ea.elapsed_time(eb), "count": r["exact"], "triangles": r["triangles"],
+                 "rel_error": (est - r["exact"]) / r["exact"] if r["exact"] else None,
+                 "rel_error_L": (est_alt - r["exact"]) / r["exact"] if r["exact"] else None}
+    peak, peak_kind = peaks()
+    # per 3-clique: the filter of w (the filters of u and v are reused by the group); per oriented edge the two
+    # list heads and the binary searches are not counted
+    alg = tri * (w["bits"] / 8)
+    achieved = alg / (ms * 1e-3) / 1e9
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        from paper_2208_11469_gb300 import synth
+        small = 14
+        srp, scl = synth.rmat(small, 16, seed=small)
+        t0 = time.perf_counter()
+        ro = O.clique4(srp.numpy(), scl.numpy(), O.EST_BF_AND, l=w["bits"], b=w["b"], seed=1)
+        dt = time.perf_counter() - t0
+        cpu = {"value": ro["triangles"] / dt, "unit": "intersections/s", "cores": 1, "kind": "oracle",
+               "sample": f"the same recipe at R-MAT scale {small} ({ro['triangles']} 3-cliques): oracle "
+                         f"orientation, oriented Bloom filters and triple-AND counts, serial C on 1 host core",
+               "seconds": dt}
+    if rank == 0:
+        line = {
+            "metric": METRIC + " (4-cliques)", "value": tri * ws / (ms * 1e-3), "unit": "intersections/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded on-device generator)",
+            "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "bloom_bits": w["bits"], "bloom_b": w["b"],
+                       "step": "orientation + oriented Bloom filters + 3-clique enumeration with triple-AND counts",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": "k_clique4 (whole step)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic_bytes": alg,
+                         "peak_source": peak_kind},
+            "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+            "results": {"triangles": tri, "est": est, "est_alt_L": est_alt, "count_sum": cs},
+            "exact_gpu": exact, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------- serving
 def serve_requests(workload, rp, cl, seed=7):
     """The request set: pair requests (sizes lognormal, half edges and half
@@ -1065,9 +1151,9 @@ def main():
     from paper_2208_11469_gb300 import pg
 
     dev = torch.device("cuda", local)
-    special = [k for k in ("batch", "serve", "jp") if k in WORKLOADS[args.workload]]
+    special = [k for k in ("batch", "serve", "jp", "clique") if k in WORKLOADS[args.workload]]
     if special:
-        {"batch": run_batch, "serve": run_serve, "jp": run_jp}[special[0]](args, ws, rank, dev)
+        {"batch": run_batch, "serve": run_serve, "jp": run_jp, "clique": run_clique}[special[0]](args, ws, rank, dev)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return

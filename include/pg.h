@@ -332,6 +332,30 @@ pg_status pg_jarvis_patrick(const pg_csr *g, const void *index, const pg_sketch 
                             double tau, void *workspace, size_t workspace_bytes, int32_t *labels,
                             pg_jp_result *out, pg_stream_t stream);
 
+/* ------------------------------------------------------------- 4-cliques --
+ * 4-clique counting (Sec. III-A, Listing "Reformulated 4-Clique Counting"):
+ * vertices ranked by (degree, id), N+_v = neighbours ranked above v; for every
+ * oriented edge u -> v, C3 = N+_u ∩ N+_v (exact), and the count is the sum
+ * over w in C3 of |N+_w ∩ C3|. With PG_EST_BF_AND / PG_EST_BF_L that
+ * innermost intersection is estimated from popcount(BF+_u AND BF+_v AND
+ * BF+_w), the Bloom filters (bits, b, seed as pg_build_bloom) being built
+ * over the oriented neighbourhoods inside the call; PG_EST_EXACT counts it.
+ *   workspace: pg_clique4_workspace_bytes(g, estimator, bits)
+ *   out:       DEVICE pg_clique4_result
+ * Errors: PG_ERR_INVALID_ARG, PG_ERR_UNSUPPORTED (estimator, bits not a
+ * multiple of 64 in [64, 1024], b not in 1..16), PG_ERR_NO_MEMORY, PG_ERR_CUDA. */
+typedef struct pg_clique4_result {
+    uint64_t triangles; /* 3-cliques (u, v, w) visited = the triangle count */
+    uint64_t exact;     /* PG_EST_EXACT: the 4-clique count; else 0 */
+    uint64_t count_sum; /* sketch: sum over the 3-cliques of the triple-AND popcount */
+    uint64_t reserved;
+    double est;         /* the 4-clique count (exact, or the chosen estimator's total) */
+    double est_alt;     /* sketch: the other Bloom estimator's total (L for AND, AND for L) */
+} pg_clique4_result;
+size_t pg_clique4_workspace_bytes(const pg_csr *g, int32_t estimator, uint32_t bits);
+pg_status pg_clique4_count(const pg_csr *g, int32_t estimator, uint32_t bits, uint32_t b, uint32_t seed,
+                           void *workspace, size_t workspace_bytes, pg_clique4_result *out, pg_stream_t stream);
+
 /* ---------------------------------------------------------------- batch --
  * Many small graphs analysed together (the per-graph Bloom-filter triangle
  * count of Sec. V, Eq. bf_int, and the LCC of Sec. II-B, per graph), in one

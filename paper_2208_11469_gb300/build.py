@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpg.so")
 SOURCES = ["pg_api.cu", "pg_index.cu", "pg_sketch.cu", "pg_intersect.cu", "pg_exact.cu", "pg_noalloc.cu",
-           "pg_batch.cu", "pg_serve.cu", "pg_cluster.cu"]
+           "pg_batch.cu", "pg_serve.cu", "pg_cluster.cu", "pg_clique.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

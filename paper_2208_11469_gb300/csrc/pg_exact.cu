@@ -276,6 +276,30 @@ cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_orient(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz, void *ws,
+                          int32_t **plus_off_out, int32_t **plus_col_out, cudaStream_t s) {
+    uint8_t *w = static_cast<uint8_t *>(ws);
+    int32_t *pos = reinterpret_cast<int32_t *>(w);
+    w += round_up(4 * (size_t)(nnz + 1), 256);
+    int32_t *plus_off = reinterpret_cast<int32_t *>(w);
+    w += round_up(4 * (size_t)(n + 1), 256);
+    int32_t *plus_col = reinterpret_cast<int32_t *>(w);
+    w += round_up(4 * (size_t)(nnz / 2 + 1), 256);
+    int32_t *scratch = reinterpret_cast<int32_t *>(w);
+    *plus_off_out = plus_off;
+    *plus_col_out = plus_col;
+    if (n == 0) {
+        launch_fill_u64(reinterpret_cast<uint64_t *>(plus_off), 1, 0, s);
+        return cudaGetLastError();
+    }
+    k_orient_flags<<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, nnz, pos);
+    cudaError_t e = launch_exclusive_scan(pos, nnz + 1, scratch, s);
+    if (e != cudaSuccess) return e;
+    k_orient_scatter<<<persistent_grid(), kThreads, 0, s>>>(row_ptr, col, n, nnz, pos, plus_off, plus_col);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32_t n,
                                const EdgeIndex &ix, const int32_t *pairs, int64_t P,
                                const EdgeOutputs &out, cudaStream_t s) {

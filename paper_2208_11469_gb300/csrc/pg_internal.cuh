@@ -170,6 +170,11 @@ size_t exact_workspace_bytes(int32_t n, int64_t nnz);
 cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
                             const int32_t *upper_off, void *ws, double *S, pg_tc_result *tc,
                             cudaStream_t s);
+// Degree orientation N+_v = {u in N_v : (d_u, u) > (d_v, v)} as a CSR, built
+// in an exact_workspace_bytes(n, nnz) workspace; the lists keep increasing
+// id order. *plus_off / *plus_col point into ws.
+cudaError_t launch_orient(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz, void *ws,
+                          int32_t **plus_off, int32_t **plus_col, cudaStream_t s);
 // Exact |N_u ∩ N_v| per upper edge (pairs == nullptr) or per pair, into
 // out.count / out.cn / out.jac.
 cudaError_t launch_exact_pairs(const int32_t *row_ptr, const int32_t *col, int32_t n,

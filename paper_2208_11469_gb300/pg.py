@@ -34,7 +34,7 @@ SYMBOLS = [
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
-    "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick",
+    "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick", "pg_clique4_workspace_bytes", "pg_clique4_count",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
     "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_submit_many", "pg_poll_many", "pg_poll",
     "pg_cancel", "pg_server_stats_get", "pg_server_destroy",
@@ -161,6 +161,8 @@ def lib() -> ctypes.CDLL:
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
                 "pg_triangle_count_noalloc": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, vp]),
                 "pg_jarvis_patrick_workspace_bytes": (sz, [P(Csr), P(SketchDesc), i32]),
+                "pg_clique4_workspace_bytes": (sz, [P(Csr), i32, u32]),
+                "pg_clique4_count": (i32, [P(Csr), i32, u32, u32, u32, vp, sz, vp, vp]),
                 "pg_jarvis_patrick": (i32, [P(Csr), vp, P(SketchDesc), i32, ctypes.c_double, vp, sz, vp, vp, vp]),
                 "pg_batch_autotune": (i32, [vp, vp, i32, ctypes.c_double, P(BatchConfig)]),
                 "pg_batch_workspace_bytes": (sz, [P(Csr), i32, vp, P(BatchConfig)]),
@@ -511,6 +513,23 @@ def jarvis_patrick(g: Graph, sk: Sketch | None, est: int, tau: float, *, labels:
         return (labels[: g.n] if want_labels else None), out
     clusters, kept, edges, _ = struct.unpack("<qqqq", bytes(out.cpu().numpy().tobytes()))
     return (labels[: g.n] if want_labels else None), {"clusters": clusters, "kept": kept, "edges": edges}
+
+
+# ---------------------------------------------------------------- 4-cliques
+def clique4_count(g: Graph, est: int, bits: int = 256, b: int = 2, seed: int = 1, *,
+                  ws: torch.Tensor | None = None, out: torch.Tensor | None = None, read: bool = True):
+    """pg_clique4_count: 4-cliques, exact or with the innermost intersection
+    estimated from Bloom filters of the oriented neighbourhoods."""
+    c = g.csr()
+    if ws is None:
+        ws = _dev_bytes(lib().pg_clique4_workspace_bytes(ctypes.byref(c), est, bits), g.device)
+    out = out if out is not None else torch.zeros(48, dtype=torch.uint8, device=g.device)
+    _check(lib().pg_clique4_count(ctypes.byref(c), est, bits, b, seed, _ptr(ws), ws.numel(), _ptr(out), _stream()),
+           "pg_clique4_count")
+    if not read:
+        return out
+    tri, exact, cs, _, e, ea = struct.unpack("<QQQQdd", bytes(out.cpu().numpy().tobytes()))
+    return {"triangles": tri, "exact": exact, "count_sum": cs, "est": e, "est_alt": ea}
 
 
 # -------------------------------------------------------------------- batch
