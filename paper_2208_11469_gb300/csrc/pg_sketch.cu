@@ -24,6 +24,7 @@ namespace {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 constexpr int kBuildThreads = 256;
+constexpr int kBloomUnroll = 4;  // 32-id chunks of a row loaded together
 
 struct HubList {
     unsigned long long *packed;  // hubs << 32 | chunks
@@ -71,7 +72,11 @@ __device__ __forceinline__ void vertex_params(const BatchMap &bm, int64_t v, uin
 
 // ---------------------------------------------------------------- Bloom --
 // Warp-private filter in shared memory (32-bit words); lanes set bits with
-// shared atomicOr, then the warp stores the row with coalesced 8-byte stores.
+// shared atomicOr, then the warp stores the row (and clears the filter for
+// the next vertex). A warp takes 32 consecutive vertices at a time: their 33
+// row offsets arrive in one coalesced load, and the first 32 neighbour ids of
+// the next vertex are fetched while the current one is hashed, so a vertex
+// costs no dependent global load (most rows are shorter than 32).
 template <int kMaxWords32>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n, uint32_t l,
@@ -83,32 +88,71 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     uint32_t *f = filt[warp];
     const int words32 = (int)(stride >> 2);  // whole row including zero padding
     if (threadIdx.x < 16) pre_s[threadIdx.x] = fmix_pre(hash_seed(seed, threadIdx.x));
+    for (int t = lane; t < words32; t += 32) f[t] = 0u;
     __syncthreads();
     HubList hubs = hub_list(hub_base);
     const int64_t warps_total = (int64_t)gridDim.x * (kBuildThreads / 32);
-    for (int64_t v = blockIdx.x * (int64_t)(kBuildThreads / 32) + warp; v < n; v += warps_total) {
-        const int32_t a = row_ptr[v], e = row_ptr[v + 1];
-        uint32_t bv = b;
-        int32_t id0 = 0;
-        vertex_params(bm, v, bv, id0);
-        for (int t = lane; t < words32; t += 32) f[t] = 0u;
-        __syncwarp();
-        if (e - a > hub_threshold) {
-            if (lane == 0) hub_append(hubs, (int32_t)v, (e - a + chunk - 1) / chunk);
-        } else {
-            for (int32_t j = a + lane; j < e; j += 32) {
-                const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - id0));
+    for (int64_t v0 = ((int64_t)blockIdx.x * (kBuildThreads / 32) + warp) * 32; v0 < n; v0 += warps_total * 32) {
+        const int cnt = (int)min((int64_t)32, (int64_t)n - v0);
+        // offsets, hash count and id offset of the 32 vertices, one per lane
+        const int32_t my_a = (int)lane < cnt ? __ldg(row_ptr + v0 + lane) : 0;
+        const int32_t my_e = (int)lane < cnt ? __ldg(row_ptr + v0 + lane + 1) : 0;
+        uint32_t my_b = b;
+        int32_t my_id0 = 0;
+        if ((int)lane < cnt) vertex_params(bm, v0 + lane, my_b, my_id0);
+        int32_t a = __shfl_sync(0xffffffffu, my_a, 0), e = __shfl_sync(0xffffffffu, my_e, 0);
+        int32_t x = (a + (int32_t)lane < e && e - a <= hub_threshold) ? __ldg(col + a + lane) : 0;
+        for (int t = 0; t < cnt; ++t) {
+            const int tn = (t + 1) & 31;
+            const int32_t an = __shfl_sync(0xffffffffu, my_a, tn), en = __shfl_sync(0xffffffffu, my_e, tn);
+            const uint32_t bv = __shfl_sync(0xffffffffu, my_b, t);
+            const int32_t id0 = __shfl_sync(0xffffffffu, my_id0, t);
+            // the next vertex's first ids, in flight while this one is hashed
+            const int32_t xn =
+                (t + 1 < cnt && an + (int32_t)lane < en && en - an <= hub_threshold) ? __ldg(col + an + lane) : 0;
+            const int32_t deg = e - a;
+            if (deg > hub_threshold) {
+                if (lane == 0) hub_append(hubs, (int32_t)(v0 + t), (deg + chunk - 1) / chunk);
+            } else if (deg > 0) {
+                if ((int32_t)lane < deg) {
+                    const uint32_t px = fmix_pre((uint32_t)(x - id0));
 #pragma unroll 4
-                for (uint32_t i = 0; i < bv; ++i) {
-                    const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
-                    atomicOr(&f[p >> 5], 1u << (p & 31u));
+                    for (uint32_t i = 0; i < bv; ++i) {
+                        const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                        atomicOr(&f[p >> 5], 1u << (p & 31u));
+                    }
+                }
+                // longer rows: four 32-id loads in flight before hashing them
+                for (int32_t j0 = a + 32; j0 < e; j0 += 32 * kBloomUnroll) {
+                    int32_t xs[kBloomUnroll];
+#pragma unroll
+                    for (int q = 0; q < kBloomUnroll; ++q) {
+                        const int32_t j = j0 + 32 * q + (int32_t)lane;
+                        xs[q] = j < e ? __ldg(col + j) : 0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kBloomUnroll; ++q) {
+                        if (j0 + 32 * q + (int32_t)lane >= e) continue;
+                        const uint32_t px = fmix_pre((uint32_t)(xs[q] - id0));
+#pragma unroll 4
+                        for (uint32_t i = 0; i < bv; ++i) {
+                            const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                            atomicOr(&f[p >> 5], 1u << (p & 31u));
+                        }
+                    }
                 }
             }
+            __syncwarp();
+            uint32_t *row = reinterpret_cast<uint32_t *>(data + (v0 + t) * stride);
+            for (int w = lane; w < words32; w += 32) {
+                row[w] = f[w];  // a hub row is stored empty here and filled by k_bloom_hub
+                f[w] = 0u;
+            }
+            __syncwarp();
+            a = an;
+            e = en;
+            x = xn;
         }
-        __syncwarp();
-        uint32_t *row = reinterpret_cast<uint32_t *>(data + v * stride);
-        for (int t = lane; t < words32; t += 32) row[t] = f[t];
-        __syncwarp();
     }
 }
 
