@@ -107,6 +107,9 @@ __global__ void __launch_bounds__(256) k_upper_lists(const int32_t *__restrict__
             const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
             const int64_t wend = c1 < (int64_t)last_end ? c1 : (int64_t)last_end;
             for (int64_t base = e; base < wend; base += 32 * kListUnroll) {
+                // three phases so that all loads of the kListUnroll edges are in flight together:
+                // locate the row and load v, then gather the degrees of v, then store
+                int32_t vs[kListUnroll], rows[kListUnroll], dus[kListUnroll];
 #pragma unroll
                 for (int j = 0; j < kListUnroll; ++j) {
                     const int64_t ee = base + 32 * j + lane;
@@ -119,13 +122,22 @@ __global__ void __launch_bounds__(256) k_upper_lists(const int32_t *__restrict__
                     const int rr = r < 31 ? r : 31;
                     const int32_t oe = __shfl_sync(0xffffffffu, off_end, rr);
                     const int32_t re = __shfl_sync(0xffffffffu, rp_end, rr);
-                    const int32_t du = __shfl_sync(0xffffffffu, deg, rr);
+                    dus[j] = __shfl_sync(0xffffffffu, deg, rr);
+                    rows[j] = rr;
+                    vs[j] = ee < wend ? __ldg(col + (re - (oe - (int32_t)ee))) : 0;
+                }
+                int32_t dvs[kListUnroll];
+#pragma unroll
+                for (int j = 0; j < kListUnroll; ++j)
+                    dvs[j] = __ldg(row_ptr + vs[j] + 1) - __ldg(row_ptr + vs[j]);
+#pragma unroll
+                for (int j = 0; j < kListUnroll; ++j) {
+                    const int64_t ee = base + 32 * j + lane;
                     if (ee < wend) {
-                        const int32_t v = __ldg(col + (re - (oe - (int32_t)ee)));
-                        eu[ee] = (int32_t)(u0 + rr);
-                        ev[ee] = v;
-                        edu[ee] = du;
-                        edv[ee] = __ldg(row_ptr + v + 1) - __ldg(row_ptr + v);
+                        eu[ee] = (int32_t)(u0 + rows[j]);
+                        ev[ee] = vs[j];
+                        edu[ee] = dus[j];
+                        edv[ee] = dvs[j];
                     }
                 }
             }
