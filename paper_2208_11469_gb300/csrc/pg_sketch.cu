@@ -71,22 +71,31 @@ __device__ __forceinline__ void vertex_params(const BatchMap &bm, int64_t v, uin
 }
 
 // ---------------------------------------------------------------- Bloom --
-// Warp-private filter in shared memory (32-bit words); lanes set bits with
-// shared atomicOr, then the warp stores the row (and clears the filter for
-// the next vertex). A warp takes 32 consecutive vertices at a time: their 33
-// row offsets arrive in one coalesced load, and the first 32 neighbour ids of
-// the next vertex are fetched while the current one is hashed, so a vertex
-// costs no dependent global load (most rows are shorter than 32).
-template <int kMaxWords32>
+// A warp takes 32 consecutive vertices at a time (their 33 row offsets in one
+// coalesced load).
+//   Short rows (at most kLaneRow ids, LANE only): each lane builds its own
+//     vertex's filter in a lane-private shared-memory column (word w of lane r
+//     at [w * 32 + r], so every access of lane r is in bank r and needs no
+//     atomic), walking its row id by id, and stores the row as 16-byte vectors.
+//   Longer rows: the warp builds one row at a time in a warp-shared filter
+//     with shared atomicOr (32 ids per step, four steps of loads in flight),
+//     fetching the next such row's first ids while hashing the current one.
+//   Hub rows (above hub_threshold): stored empty here and filled by
+//     k_bloom_hub.
+constexpr int32_t kLaneRow = 32;
+
+template <int kMaxWords32, bool LANE>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n, uint32_t l,
     uint32_t b, uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t hub_threshold,
     int32_t chunk, int32_t *hub_base, BatchMap bm) {
     __shared__ uint32_t filt[kBuildThreads / 32][kMaxWords32];
     __shared__ uint32_t pre_s[16];
+    extern __shared__ uint32_t lane_filters[];  // LANE: [warps][words32][32]
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint32_t *f = filt[warp];
     const int words32 = (int)(stride >> 2);  // whole row including zero padding
+    uint32_t *lf = lane_filters + (size_t)warp * words32 * 32 + lane;
     if (threadIdx.x < 16) pre_s[threadIdx.x] = fmix_pre(hash_seed(seed, threadIdx.x));
     for (int t = lane; t < words32; t += 32) f[t] = 0u;
     __syncthreads();
@@ -100,16 +109,35 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
         uint32_t my_b = b;
         int32_t my_id0 = 0;
         if ((int)lane < cnt) vertex_params(bm, v0 + lane, my_b, my_id0);
-        int32_t a = __shfl_sync(0xffffffffu, my_a, 0), e = __shfl_sync(0xffffffffu, my_e, 0);
+        const bool mine = LANE && (int)lane < cnt && my_e - my_a <= kLaneRow;
+        if (mine) {
+            for (int w = 0; w < words32; ++w) lf[w * 32] = 0u;
+            for (int32_t j = my_a; j < my_e; ++j) {
+                const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - my_id0));
+                for (uint32_t i = 0; i < my_b; ++i) {
+                    const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                    lf[(p >> 5) * 32] |= 1u << (p & 31u);
+                }
+            }
+            uint4 *row4 = reinterpret_cast<uint4 *>(data + (v0 + lane) * stride);
+            for (int q = 0; q < words32 / 4; ++q)
+                row4[q] = make_uint4(lf[(4 * q) * 32], lf[(4 * q + 1) * 32], lf[(4 * q + 2) * 32], lf[(4 * q + 3) * 32]);
+        }
+        // the other vertices of the batch, one warp-wide row at a time
+        unsigned rest = __ballot_sync(0xffffffffu, (int)lane < cnt && !mine);
+        if (!rest) continue;
+        int t = __ffs(rest) - 1;
+        int32_t a = __shfl_sync(0xffffffffu, my_a, t), e = __shfl_sync(0xffffffffu, my_e, t);
         int32_t x = (a + (int32_t)lane < e && e - a <= hub_threshold) ? __ldg(col + a + lane) : 0;
-        for (int t = 0; t < cnt; ++t) {
-            const int tn = (t + 1) & 31;
+        while (true) {
+            rest &= rest - 1;
+            const int tn = rest ? __ffs(rest) - 1 : 0;
             const int32_t an = __shfl_sync(0xffffffffu, my_a, tn), en = __shfl_sync(0xffffffffu, my_e, tn);
             const uint32_t bv = __shfl_sync(0xffffffffu, my_b, t);
             const int32_t id0 = __shfl_sync(0xffffffffu, my_id0, t);
-            // the next vertex's first ids, in flight while this one is hashed
+            // the next row's first ids, in flight while this one is hashed
             const int32_t xn =
-                (t + 1 < cnt && an + (int32_t)lane < en && en - an <= hub_threshold) ? __ldg(col + an + lane) : 0;
+                (rest && an + (int32_t)lane < en && en - an <= hub_threshold) ? __ldg(col + an + lane) : 0;
             const int32_t deg = e - a;
             if (deg > hub_threshold) {
                 if (lane == 0) hub_append(hubs, (int32_t)(v0 + t), (deg + chunk - 1) / chunk);
@@ -149,6 +177,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
                 f[w] = 0u;
             }
             __syncwarp();
+            if (!rest) break;
+            t = tn;
             a = an;
             e = en;
             x = xn;
@@ -469,14 +499,16 @@ cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32
     const int grid = build_grid(n);
     const int hub_grid = device_info().sm_count * 4;
     if (stride <= 128) {
-        k_bloom_warp<32><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
-                                                        kBloomHub, kBloomChunk, hub_base, bm);
+        // lane-private filters for short rows: words x 32 lanes x warps
+        const size_t lane_smem = (size_t)(stride / 4) * 32 * (kBuildThreads / 32) * 4;
+        k_bloom_warp<32, true><<<grid, kBuildThreads, lane_smem, s>>>(row_ptr, col, n, l, b, seed, data, stride,
+                                                                      kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<32><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
                                                            kBloomChunk, hub_base, bm);
         note_launch(2);
     } else {
-        k_bloom_warp<256><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
-                                                         kBloomHub, kBloomChunk, hub_base, bm);
+        k_bloom_warp<256, false><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
+                                                                kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<256><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
                                                             kBloomChunk, hub_base, bm);
         note_launch(2);
