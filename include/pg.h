@@ -170,6 +170,20 @@ pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *workspace,
 pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *workspace,
                            size_t workspace_bytes, pg_stream_t stream);
 
+/* Sketch files (checkpoint / resume of the sketches, which are a pure
+ * function of the CSR, the parameters and the seed): a 64-byte header
+ * {"PGSKTCH1", version 1, kind, bits, b, k, seed, n, stride, n * stride}
+ * followed by the n rows exactly as they lie in device memory.
+ * pg_sketch_save synchronises the stream and writes sk->data (DEVICE) to path.
+ * pg_sketch_load_header fills every field of *sk but data from the file.
+ * pg_sketch_load synchronises the stream and copies the rows into sk->data
+ * (DEVICE, n * stride bytes) if the file's descriptor equals *sk's.
+ * Errors: PG_ERR_NOT_FOUND (file cannot be opened), PG_ERR_INVALID_ARG (bad
+ * header, descriptor mismatch, truncated or unwritable file), PG_ERR_CUDA. */
+pg_status pg_sketch_save(const pg_sketch *sk, const char *path, pg_stream_t stream);
+pg_status pg_sketch_load_header(const char *path, pg_sketch *sk);
+pg_status pg_sketch_load(pg_sketch *sk, const char *path, pg_stream_t stream);
+
 /* --------------------------------------------------------------- estimators */
 #define PG_EST_EXACT       0 /* exact |N_u ∩ N_v| (no sketch) */
 #define PG_EST_BF_AND      1 /* Eq. (bf_int) on popcount(B_u AND B_v), B1 = l read as l - 1 */

@@ -1,9 +1,11 @@
 // The C ABI of include/pg.h: argument checks, workspace carving, launches.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "pg_internal.cuh"
 
@@ -199,6 +201,7 @@ uint64_t pg_kernel_launches(void) { return g_launches.load(std::memory_order_rel
 
 pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *result,
                           pg_stream_t stream) {
+    PG_TRACE("pg_validate_csr");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(result != nullptr && (reinterpret_cast<uintptr_t>(result) & 7u) == 0,
@@ -217,6 +220,7 @@ const int32_t *pg_edge_index_upper_off(const void *index) {
 }
 
 pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes, pg_stream_t stream) {
+    PG_TRACE("pg_build_edge_index");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(index != nullptr && aligned16(index), PG_ERR_INVALID_ARG,
@@ -263,6 +267,7 @@ static pg_status build_common(const pg_csr *g, const pg_sketch *sk, void *ws, si
 
 pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *ws, size_t ws_bytes,
                          pg_stream_t stream) {
+    PG_TRACE("pg_build_bloom");
     pg_status st = build_common(g, sk, ws, ws_bytes);
     if (st) return st;
     PG_REQUIRE(sk->kind == PG_SK_BLOOM, PG_ERR_INVALID_ARG, "pg_build_bloom needs kind PG_SK_BLOOM");
@@ -275,6 +280,7 @@ pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *ws, size_t 
 
 pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *ws, size_t ws_bytes,
                            pg_stream_t stream) {
+    PG_TRACE("pg_build_minhash");
     pg_status st = build_common(g, sk, ws, ws_bytes);
     if (st) return st;
     if (sk->kind == PG_SK_KHASH) {
@@ -307,6 +313,7 @@ size_t pg_workspace_bytes(const pg_csr *g, const pg_sketch *sk, int32_t estimato
 pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch *sk,
                             int32_t estimator, void *ws, size_t ws_bytes, pg_tc_result *out,
                             pg_stream_t stream) {
+    PG_TRACE("pg_triangle_count");
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
     if (st) return st;
@@ -334,6 +341,7 @@ pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch 
 pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
                         void *ws, size_t ws_bytes, float *lcc, double *tri, pg_tc_result *tc,
                         pg_stream_t stream) {
+    PG_TRACE("pg_clustering");
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
     if (st) return st;
@@ -383,6 +391,7 @@ static pg_status pairs_common(const pg_csr *g, const void *index, const pg_sketc
 pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *sk,
                            int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
                            size_t ws_bytes, float *cn, float *jac, pg_stream_t stream) {
+    PG_TRACE("pg_jaccard_pairs");
     Workspace w;
     pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
     if (st) return st;
@@ -404,6 +413,7 @@ pg_status pg_jaccard_pairs(const pg_csr *g, const void *index, const pg_sketch *
 pg_status pg_similarity_pairs(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
                               const int32_t *pairs, int64_t P, void *ws, size_t ws_bytes,
                               const pg_similarity *out, pg_stream_t stream) {
+    PG_TRACE("pg_similarity_pairs");
     Workspace w;
     pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
     if (st) return st;
@@ -433,6 +443,7 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
                          int32_t estimator, const int32_t *pairs, int64_t P, void *ws,
                          size_t ws_bytes, int32_t *count, int32_t *aux, uint64_t *hist,
                          pg_stream_t stream) {
+    PG_TRACE("pg_edge_counts");
     Workspace w;
     pg_status st = pairs_common(g, index, sk, estimator, pairs, P, ws, ws_bytes, &w);
     if (st) return st;
@@ -459,6 +470,7 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
 
 pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
                      void *ws, size_t ws_bytes, const pg_outputs *out, pg_stream_t stream) {
+    PG_TRACE("pg_analyze");
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
     if (st) return st;
@@ -515,6 +527,126 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
         if (out->tc) PG_TRY_CUDA(launch_tc_finalize(hist, *sk, estimator, out->tc, stream), "pg_analyze");
     }
     if (S) PG_TRY_CUDA(launch_lcc_finalize(g->row_ptr, g->n, S, out->lcc, out->tri, stream), "pg_analyze");
+    return PG_OK;
+}
+
+// ------------------------------------------------------------ sketch files
+// A sketch file is a 64-byte header followed by the n rows of stride bytes,
+// as they lie in device memory.
+namespace {
+struct SketchFileHeader {
+    char magic[8];  // "PGSKTCH1"
+    int32_t version;
+    int32_t kind;
+    uint32_t bits, b, k, seed;
+    int32_t n;
+    int32_t pad;
+    int64_t stride;
+    int64_t bytes;  // n * stride
+    uint8_t reserved[8];
+};
+static_assert(sizeof(SketchFileHeader) == 64, "sketch file header is 64 bytes");
+constexpr char kSketchMagic[8] = {'P', 'G', 'S', 'K', 'T', 'C', 'H', '1'};
+constexpr size_t kFileChunk = 64u << 20;
+
+pg_status read_header(const char *path, SketchFileHeader *h, FILE **fp) {
+    PG_REQUIRE(path != nullptr, PG_ERR_INVALID_ARG, "sketch file path is NULL");
+    FILE *f = std::fopen(path, "rb");
+    PG_REQUIRE(f != nullptr, PG_ERR_NOT_FOUND, "cannot open sketch file %s", path);
+    const bool ok = std::fread(h, sizeof(*h), 1, f) == 1 && std::memcmp(h->magic, kSketchMagic, 8) == 0 &&
+                    h->version == 1 && h->n >= 0 && h->stride >= 0 && h->bytes == (int64_t)h->n * h->stride &&
+                    (h->kind == PG_SK_BLOOM || h->kind == PG_SK_KHASH || h->kind == PG_SK_1HASH);
+    if (!ok) {
+        std::fclose(f);
+        return set_error(PG_ERR_INVALID_ARG, "%s is not a sketch file (bad header)", path);
+    }
+    if (fp)
+        *fp = f;
+    else
+        std::fclose(f);
+    return PG_OK;
+}
+}  // namespace
+
+pg_status pg_sketch_save(const pg_sketch *sk, const char *path, pg_stream_t stream) {
+    PG_TRACE("pg_sketch_save");
+    PG_REQUIRE(sk != nullptr && path != nullptr && (sk->n == 0 || sk->data != nullptr), PG_ERR_INVALID_ARG,
+               "pg_sketch_save: NULL argument");
+    PG_REQUIRE(sk->n >= 0 && sk->stride_bytes > 0, PG_ERR_INVALID_ARG, "pg_sketch_save: bad descriptor");
+    SketchFileHeader h{};
+    std::memcpy(h.magic, kSketchMagic, 8);
+    h.version = 1;
+    h.kind = sk->kind;
+    h.bits = sk->bits;
+    h.b = sk->b;
+    h.k = sk->k;
+    h.seed = sk->seed;
+    h.n = sk->n;
+    h.stride = sk->stride_bytes;
+    h.bytes = (int64_t)sk->n * sk->stride_bytes;
+    PG_TRY_CUDA(cudaStreamSynchronize(stream), "pg_sketch_save: stream");
+    FILE *f = std::fopen(path, "wb");
+    PG_REQUIRE(f != nullptr, PG_ERR_NOT_FOUND, "pg_sketch_save: cannot create %s", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    std::vector<uint8_t> buf(ok && h.bytes ? std::min<size_t>(kFileChunk, (size_t)h.bytes) : 0);
+    cudaError_t e = cudaSuccess;
+    for (int64_t off = 0; ok && e == cudaSuccess && off < h.bytes; off += (int64_t)buf.size()) {
+        const size_t len = std::min<size_t>(buf.size(), (size_t)(h.bytes - off));
+        e = cudaMemcpy(buf.data(), static_cast<const uint8_t *>(sk->data) + off, len, cudaMemcpyDeviceToHost);
+        ok = e == cudaSuccess && std::fwrite(buf.data(), 1, len, f) == len;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (e != cudaSuccess) return cuda_status(e, "pg_sketch_save");
+    PG_REQUIRE(ok, PG_ERR_INVALID_ARG, "pg_sketch_save: writing %s failed", path);
+    return PG_OK;
+}
+
+pg_status pg_sketch_load_header(const char *path, pg_sketch *sk) {
+    PG_REQUIRE(sk != nullptr, PG_ERR_INVALID_ARG, "pg_sketch_load_header: sketch is NULL");
+    SketchFileHeader h{};
+    pg_status st = read_header(path, &h, nullptr);
+    if (st) return st;
+    sk->kind = h.kind;
+    sk->bits = h.bits;
+    sk->b = h.b;
+    sk->k = h.k;
+    sk->seed = h.seed;
+    sk->n = h.n;
+    sk->stride_bytes = h.stride;
+    return PG_OK;
+}
+
+pg_status pg_sketch_load(pg_sketch *sk, const char *path, pg_stream_t stream) {
+    PG_TRACE("pg_sketch_load");
+    PG_REQUIRE(sk != nullptr && (sk->n == 0 || sk->data != nullptr), PG_ERR_INVALID_ARG,
+               "pg_sketch_load: NULL argument");
+    SketchFileHeader h{};
+    FILE *f = nullptr;
+    pg_status st = read_header(path, &h, &f);
+    if (st) return st;
+    const bool same = h.kind == sk->kind && h.bits == sk->bits && h.b == sk->b && h.k == sk->k &&
+                      h.seed == sk->seed && h.n == sk->n && h.stride == sk->stride_bytes;
+    if (!same) {
+        std::fclose(f);
+        return set_error(PG_ERR_INVALID_ARG,
+                         "pg_sketch_load: %s holds kind %d bits %u b %u k %u seed %u n %d stride %lld, the "
+                         "descriptor differs",
+                         path, h.kind, h.bits, h.b, h.k, h.seed, h.n, (long long)h.stride);
+    }
+    cudaError_t e = cudaStreamSynchronize(stream);
+    std::vector<uint8_t> buf(h.bytes ? std::min<size_t>(kFileChunk, (size_t)h.bytes) : 0);
+    bool ok = e == cudaSuccess;
+    for (int64_t off = 0; ok && off < h.bytes; off += (int64_t)buf.size()) {
+        const size_t len = std::min<size_t>(buf.size(), (size_t)(h.bytes - off));
+        ok = std::fread(buf.data(), 1, len, f) == len;
+        if (ok) {
+            e = cudaMemcpy(static_cast<uint8_t *>(sk->data) + off, buf.data(), len, cudaMemcpyHostToDevice);
+            ok = e == cudaSuccess;
+        }
+    }
+    std::fclose(f);
+    if (e != cudaSuccess) return cuda_status(e, "pg_sketch_load");
+    PG_REQUIRE(ok, PG_ERR_INVALID_ARG, "pg_sketch_load: %s is truncated", path);
     return PG_OK;
 }
 

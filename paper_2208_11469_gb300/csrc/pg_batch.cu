@@ -264,6 +264,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
                           pg_batch_config *cfg_host, uint32_t seed, void *workspace, size_t workspace_bytes,
                           pg_tc_result *tc_out, float *lcc_out, double *tri_out, pg_stream_t stream,
                           pg_batch **out) {
+    PG_TRACE("pg_batch_create");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(out != nullptr, PG_ERR_INVALID_ARG, "pg_batch_create: out is NULL");
@@ -371,6 +372,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
 }
 
 pg_status pg_batch_run(pg_batch *bt, pg_stream_t stream) {
+    PG_TRACE("pg_batch_run");
     PG_REQUIRE(bt != nullptr, PG_ERR_INVALID_ARG, "pg_batch_run: batch is NULL");
     cudaStream_t s = stream;
     if (s == nullptr) {  // the legacy default stream cannot be captured: run eagerly

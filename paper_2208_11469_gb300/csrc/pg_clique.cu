@@ -224,6 +224,7 @@ size_t pg_clique4_workspace_bytes(const pg_csr *g, int32_t estimator, uint32_t b
 
 pg_status pg_clique4_count(const pg_csr *g, int32_t estimator, uint32_t bits, uint32_t b, uint32_t seed,
                            void *workspace, size_t workspace_bytes, pg_clique4_result *out, pg_stream_t stream) {
+    PG_TRACE("pg_clique4_count");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(estimator == PG_EST_EXACT || estimator == PG_EST_BF_AND || estimator == PG_EST_BF_L,

@@ -198,6 +198,7 @@ size_t pg_jarvis_patrick_workspace_bytes(const pg_csr *g, const pg_sketch *sk, i
 pg_status pg_jarvis_patrick(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator, double tau,
                             void *workspace, size_t workspace_bytes, int32_t *labels, pg_jp_result *out,
                             pg_stream_t stream) {
+    PG_TRACE("pg_jarvis_patrick");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(estimator >= PG_EST_EXACT && estimator <= PG_EST_1H_LITERAL, PG_ERR_INVALID_ARG,

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/pg.h"
@@ -21,6 +22,16 @@ pg_status cuda_status(cudaError_t e, const char *what);
     do {                                                                          \
         if (!(cond)) return ::pg::set_error(st, __VA_ARGS__);                     \
     } while (0)
+
+// NVTX range around an entry point (visible in Nsight tools; no cost when no
+// tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define PG_TRACE(name) ::pg::TraceRange pg_trace_range_(name)
 
 // Argument checks shared by the entry points (pg_api.cu).
 pg_status check_graph(const pg_csr *g);

@@ -879,6 +879,7 @@ size_t pg_server_reserved_bytes(const pg_csr *g, const pg_server_opts *opts) {
 
 pg_status pg_server_create(const pg_csr *g, const pg_sketch *const *sketches, int32_t n_sketches, void *arena,
                            size_t arena_bytes, const pg_server_opts *opts, pg_server **out) {
+    PG_TRACE("pg_server_create");
     pg_status st = check_graph(g);
     if (st) return st;
     PG_REQUIRE(out != nullptr, PG_ERR_INVALID_ARG, "pg_server_create: out is NULL");
@@ -1224,6 +1225,7 @@ pg_status pg_server_stats_get(pg_server *sv, pg_server_stats *out) {
 }
 
 pg_status pg_server_destroy(pg_server *sv) {
+    PG_TRACE("pg_server_destroy");
     if (!sv) return PG_OK;
     {
         std::lock_guard<std::mutex> lk(sv->mu);

@@ -32,6 +32,7 @@ SYMBOLS = [
     "pg_status_string", "pg_last_error", "pg_version", "pg_validate_csr", "pg_edge_index_bytes",
     "pg_build_edge_index", "pg_edge_index_upper_off", "pg_sketch_stride",
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
+    "pg_sketch_save", "pg_sketch_load_header", "pg_sketch_load",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick", "pg_clique4_workspace_bytes", "pg_clique4_count",
@@ -150,6 +151,9 @@ def lib() -> ctypes.CDLL:
                 "pg_build_workspace_bytes": (sz, [P(Csr)]),
                 "pg_build_bloom": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
                 "pg_build_minhash": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
+                "pg_sketch_save": (i32, [P(SketchDesc), ctypes.c_char_p, vp]),
+                "pg_sketch_load_header": (i32, [ctypes.c_char_p, P(SketchDesc)]),
+                "pg_sketch_load": (i32, [P(SketchDesc), ctypes.c_char_p, vp]),
                 "pg_hist_bins": (i64, [P(SketchDesc), i32]),
                 "pg_workspace_bytes": (sz, [P(Csr), P(SketchDesc), i32]),
                 "pg_triangle_count": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, vp, vp]),
@@ -316,6 +320,23 @@ def alloc_sketch(g: Graph, kind: int, *, bits: int = 0, b: int = 0, k: int = 0, 
     st = sketch_stride(kind, bits, k) if stride is None else int(stride)
     data = _dev_bytes(g.n * st, g.device)
     return Sketch(kind, bits, b, k, seed, g.n, st, data)
+
+
+def sketch_save(sk: Sketch, path: str) -> None:
+    """pg_sketch_save: write the sketch rows and descriptor to a file."""
+    d = sk.desc()
+    _check(lib().pg_sketch_save(ctypes.byref(d), os.fsencode(path), _stream()), "pg_sketch_save")
+
+
+def sketch_load(path: str, device="cuda") -> Sketch:
+    """pg_sketch_load_header + pg_sketch_load: a sketch read back from a file."""
+    d = SketchDesc()
+    _check(lib().pg_sketch_load_header(os.fsencode(path), ctypes.byref(d)), "pg_sketch_load_header")
+    data = _dev_bytes(d.n * d.stride_bytes, torch.device(device))
+    sk = Sketch(d.kind, d.bits, d.b, d.k, d.seed, d.n, d.stride_bytes, data)
+    d2 = sk.desc()
+    _check(lib().pg_sketch_load(ctypes.byref(d2), os.fsencode(path), _stream()), "pg_sketch_load")
+    return sk
 
 
 def build_workspace_bytes(g: Graph) -> int:

@@ -109,3 +109,25 @@ def test_argument_errors_return_codes(L):
     # odd pairs pointer
     assert L.pg_jaccard_pairs(byref(g), None, byref(sk), pg.EST_KH, ctypes.c_void_p(0x8004), 3,
                               ctypes.c_void_p(0x7000), need, None, None, None) == -1
+
+
+def test_sketch_file_header_errors(tmp_path):
+    """pg_sketch_load_header is host-only: a missing file, a file that is not
+    a sketch and a truncated header are refused with the documented codes."""
+    import ctypes
+    from paper_2208_11469_gb300 import pg
+    L = pg.lib()
+    d = pg.SketchDesc()
+    assert L.pg_sketch_load_header(str(tmp_path / "none.pgs").encode(), ctypes.byref(d)) == -7
+    bad = tmp_path / "bad.pgs"
+    bad.write_bytes(b"NOTASKETCH" + bytes(100))
+    assert L.pg_sketch_load_header(str(bad).encode(), ctypes.byref(d)) == -1
+    short = tmp_path / "short.pgs"
+    short.write_bytes(b"PGSKTCH1" + bytes(10))
+    assert L.pg_sketch_load_header(str(short).encode(), ctypes.byref(d)) == -1
+    # a well-formed header (as pg_sketch_save writes it) is read back field by field
+    import struct
+    good = tmp_path / "good.pgs"
+    good.write_bytes(struct.pack("<8siiIIIIiiqq8s", b"PGSKTCH1", 1, 1, 448, 2, 0, 7, 3, 0, 64, 192, bytes(8)))
+    assert L.pg_sketch_load_header(str(good).encode(), ctypes.byref(d)) == 0
+    assert (d.kind, d.bits, d.b, d.k, d.seed, d.n, d.stride_bytes) == (1, 448, 2, 0, 7, 3, 64)

@@ -297,3 +297,23 @@ def test_validate_csr_reports_malformed_graphs(pg):
     rp3 = rp.clone()
     rp3[-1] += 1
     assert pg.validate_csr(pg.Graph(rp3.cuda(), cl.cuda()))[0] == "bad_row_ptr"
+
+
+def test_sketch_file_round_trip(pg, tmp_path):
+    """A saved sketch loads back bit for bit and gives the same counts; a file
+    whose descriptor differs from the target is refused."""
+    g, rp, cl = _dev(pg, "rmat12")
+    for sk in (pg.build_bloom(g, 448, 2, seed=3), pg.build_minhash(g, pg.SK_KHASH, 64, seed=3),
+               pg.build_minhash(g, pg.SK_1HASH, 32, seed=3)):
+        path = str(tmp_path / f"s{sk.kind}.pgs")
+        pg.sketch_save(sk, path)
+        back = pg.sketch_load(path)
+        assert (back.kind, back.bits, back.b, back.k, back.seed, back.n, back.stride) == \
+            (sk.kind, sk.bits, sk.b, sk.k, sk.seed, sk.n, sk.stride)
+        assert torch.equal(back.data[: g.n * sk.stride], sk.data[: g.n * sk.stride])
+        est = {pg.SK_BLOOM: pg.EST_BF_AND, pg.SK_KHASH: pg.EST_KH, pg.SK_1HASH: pg.EST_1H}[sk.kind]
+        assert pg.triangle_count(g, back, est) == pg.triangle_count(g, sk, est)
+    other = pg.alloc_sketch(g, pg.SK_BLOOM, bits=448, b=1, seed=3)
+    d = other.desc()
+    import ctypes
+    assert pg.lib().pg_sketch_load(ctypes.byref(d), str(tmp_path / f"s{pg.SK_BLOOM}.pgs").encode(), None) == -1
