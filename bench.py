@@ -1015,7 +1015,6 @@ def run_serve(args, ws, rank, dev):
 
     # one request per launch: each pair request alone through pg_jaccard_pairs (same pass kernels)
     per = []
-    pin = {}
     t0 = time.perf_counter()
     n_single = 0
     for kind, x in reqs:
