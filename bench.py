@@ -618,7 +618,7 @@ def run_batch(args, ws, rank, dev):
     achieved = alg / (ms_max * 1e-3) / 1e9
     buckets = {}
     for c, v in zip(cfg, batch.variants):
-        buckets.setdefault(f"{c[0]}b{c[1]}", {"graphs": 0, "lanes": v})["graphs"] += 1
+        buckets.setdefault(f"{c[0]}b{c[1]}", {"graphs": 0, "groups_per_chunk": v})["graphs"] += 1
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws, "steps": args.steps,

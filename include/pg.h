@@ -382,10 +382,12 @@ pg_status pg_clique4_count(const pg_csr *g, int32_t estimator, uint32_t bits, ui
  * sketch and estimates are the same in the batch and alone.
  *
  * Per graph i, cfg[i] sets the Bloom filter: bits in {64, 128, 256, 512,
- * 1024}, b in [1, 16], and variant = lanes per sketch row of the pass (0 =
- * let pg_batch_create time the candidates and choose; it writes the choice
- * back into cfg). Graphs with equal (bits, b) must be contiguous: order them
- * by bucket. */
+ * 1024}, b in [1, 16], and variant in [0, 1024] = consecutive 32-vertex
+ * groups per warp work chunk of the pass (0 = let pg_batch_create time the
+ * candidates 1, 4, 16 and choose; it writes the choice back into cfg). Every
+ * variant gives bit-identical results: the per-vertex sums are exact
+ * fixed-point sums. Graphs with equal (bits, b) must be contiguous: order
+ * them by bucket. */
 typedef struct pg_batch_config {
     uint32_t bits;
     uint32_t b;
@@ -404,8 +406,8 @@ typedef struct pg_batch pg_batch;
 pg_status pg_batch_autotune(const int32_t *n, const int64_t *nnz, int32_t graphs, double budget,
                             pg_batch_config *cfg);
 
-/* Device workspace a batch needs (edge index, graph tables, per-graph
- * histograms, sketches, per-vertex sums); 0 for invalid arguments. */
+/* Device workspace a batch needs (graph tables, per-graph histograms,
+ * estimator tables, sketches); 0 for invalid arguments. */
 size_t pg_batch_workspace_bytes(const pg_csr *g, int32_t graphs, const int32_t *voff,
                                 const pg_batch_config *cfg);
 
@@ -416,14 +418,14 @@ size_t pg_batch_workspace_bytes(const pg_csr *g, int32_t graphs, const int32_t *
  * tri double [n] or NULL (per vertex, as pg_clustering). Synchronises the
  * stream; when a variant is 0 it runs and times the candidate passes once.
  * Errors: PG_ERR_INVALID_ARG (NULLs, voff not covering g, non-contiguous
- * buckets, b out of range), PG_ERR_UNSUPPORTED (bits), PG_ERR_NO_MEMORY
+ * buckets, b or variant out of range), PG_ERR_UNSUPPORTED (bits), PG_ERR_NO_MEMORY
  * (workspace too small), PG_ERR_CUDA. On error *out is unchanged. */
 pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff, pg_batch_config *cfg,
                           uint32_t seed, void *workspace, size_t workspace_bytes, pg_tc_result *tc,
                           float *lcc, double *tri, pg_stream_t stream, pg_batch **out);
 
-/* One run: edge index, sketches and pass of every graph, then LCC and the
- * per-graph triangle counts. On a non-default stream the first run captures
+/* One run: sketches and pass of every graph (the pass writes LCC and
+ * triangles per vertex), then the per-graph triangle counts. On a non-default stream the first run captures
  * the sequence as a CUDA graph (for that stream) and every run launches it;
  * on the default stream (NULL) the kernels are launched one by one. The CSR
  * contents may change between runs (same n, nnz and voff). Asynchronous. */

@@ -4,20 +4,18 @@
 // graph g owns vertices [voff[g], voff[g+1])). Each graph gets its own Bloom
 // parameters (l, b) and kernel variant; graphs with equal (l, b) must be
 // contiguous ("buckets"). One run is
-//   upper-edge index of the union graph
-//   -> per bucket: Bloom build of its vertex range (hashing each graph's own
-//      ids, so a sketch is the same alone and in the batch)
-//   -> per bucket: fused Bloom pass (per-graph popcount histograms, per-vertex
-//      sums)
-//   -> LCC of every vertex, and per graph the histogram dot (TC estimate).
+//   per bucket: Bloom build of its vertex range (hashing each graph's own
+//     ids, so a sketch is the same alone and in the batch)
+//   -> per bucket: pull pass over the rows of its vertices (per-graph
+//      popcount histograms, per-vertex sums, LCC and triangles per vertex)
+//   -> per graph the histogram dot (TC estimate).
 // The first pg_batch_run on a non-default stream captures this sequence into
 // a CUDA graph; later runs replay it with one launch.
 //
 // The autotuner (pg_batch_autotune) picks per graph the filter length from
 // the storage budget (Sec. V-A), the hash count from an accuracy model of the
-// AND estimator (Eq. bf_int), and pg_batch_create times the lane mappings
-// available for each bucket's width on the bucket itself and keeps the
-// fastest.
+// AND estimator (Eq. bf_int), and pg_batch_create times the pull pass's
+// lane/warp split on each bucket itself and keeps the fastest.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -27,6 +25,216 @@
 
 namespace pg {
 namespace {
+
+// ------------------------------------------------------------- pull pass
+// The pass walks each vertex's whole row (every undirected edge is seen from
+// both ends, so no upper-edge list is built): for vertex u of graph g,
+//   S_u = sum over v in N(u), v != u, of est(|B_u AND B_v|)   (Eq. bf_int,
+//         the same per-edge estimate as the edge pass; S_u is twice the
+//         estimated triangles at u)
+//   hist_g[|B_u AND B_v|] += 1 for every v > u   (each upper edge once)
+// and from S_u directly lcc_u = S_u / (d_u (d_u - 1)) and tri_u = S_u / 2.
+// S_u is an exact 128-bit sum of the table's fixed-point estimates, so it
+// does not depend on the order of the adds or on the work mapping.
+//
+// Work order: 32-vertex groups (row r of a group is held by lane r), `chunk`
+// consecutive groups per warp chunk, chunks dealt to the warps round-robin so
+// that at any time the warps work inside a window of a few graphs whose
+// sketch rows stay in L2. A warp walks its group's entries (the rows are
+// contiguous in the CSR) 32 at a time, one entry per lane with coalesced
+// loads whatever the degrees: a 5-step search over the row ends held by the
+// lanes gives each entry's row, and one inclusive warp scan of the 32
+// fixed-point estimates gives each row its part of the step. Each warp keeps
+// a shared-memory histogram for the graph it is in and flushes it (one
+// global atomic per non-zero bin) when it moves to another graph.
+constexpr int kPullThreads = 256;
+constexpr int kPullWarps = kPullThreads / 32;
+
+struct PullParams {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    int32_t v_lo, v_hi;              // the bucket's vertices
+    const uint8_t *data;             // sketch rows addressed by global vertex id
+    int64_t stride;
+    uint32_t l;
+    const unsigned long long *tabV;  // fixed-point estimates by popcount [l + 1]
+    const int32_t *gid;
+    const int64_t *hoff;
+    unsigned long long *hist;        // per-graph histograms (zeroed before the pass)
+    float *lcc;
+    double *tri;                     // or null
+    int32_t chunk;                   // groups per warp chunk
+};
+
+// The W payload words of a sketch row (W = l / 32: 2 for 64-bit filters, whose
+// 16-byte rows end in zero padding, else a multiple of 4).
+template <int W>
+struct Row {
+    uint32_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Row<W> pull_row(const PullParams &p, int32_t v) {
+    // a column naming a vertex outside the bucket (not a block-diagonal input) reads a row of the bucket
+    v = min(max(v, p.v_lo), p.v_hi - 1);
+    const uint8_t *src = p.data + (int64_t)v * p.stride;
+    Row<W> r;
+    if (W == 2) {
+        const uint2 x = __ldg(reinterpret_cast<const uint2 *>(src));
+        r.w[0] = x.x;
+        r.w[1] = x.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) {
+            const uint4 x = __ldg(reinterpret_cast<const uint4 *>(src) + q);
+            r.w[4 * q] = x.x;
+            r.w[4 * q + 1] = x.y;
+            r.w[4 * q + 2] = x.z;
+            r.w[4 * q + 3] = x.w;
+        }
+    }
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t and_popc(const Row<W> &a, const Row<W> &b) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) c += __popc(a.w[q] & b.w[q]);
+    return c;
+}
+
+// 128-bit accumulator: lo + 2^64 hi.
+__device__ __forceinline__ void acc_add(unsigned long long &lo, uint32_t &hi, unsigned long long x) {
+    lo += x;
+    hi += lo < x;
+}
+
+__device__ __forceinline__ void flush_hist(const PullParams &p, uint32_t *hw, int32_t g, unsigned lane) {
+    __syncwarp();
+    if (g >= 0) {
+        unsigned long long *dst = p.hist + __ldg(p.hoff + g);
+        for (uint32_t i = lane; i <= p.l; i += 32) {
+            const uint32_t x = hw[i];
+            if (x) {
+                atomicAdd(dst + i, (unsigned long long)x);
+                hw[i] = 0u;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int W>
+__global__ void __launch_bounds__(kPullThreads) k_batch_pull(PullParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int32_t len = (int32_t)p.l + 1;
+    unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *hw = reinterpret_cast<uint32_t *>(smem + 8 * (size_t)len) + (size_t)(threadIdx.x >> 5) * len;
+    for (int32_t i = threadIdx.x; i < len; i += blockDim.x) tabV[i] = p.tabV[i];
+    for (int32_t i = threadIdx.x; i < len * kPullWarps; i += blockDim.x)
+        reinterpret_cast<uint32_t *>(smem + 8 * (size_t)len)[i] = 0u;
+    __syncthreads();
+
+    const unsigned lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * kPullThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * kPullWarps;
+    const int64_t groups = ((int64_t)p.v_hi - p.v_lo + 31) / 32;
+    const int64_t chunks = (groups + p.chunk - 1) / p.chunk;
+    int32_t warp_g = -1;  // graph of the warp's shared histogram
+
+    for (int64_t ch = warp; ch < chunks; ch += warps) {
+        for (int gi = 0; gi < p.chunk; ++gi) {
+            const int64_t grp = ch * p.chunk + gi;
+            if (grp >= groups) break;
+            const int32_t v0 = p.v_lo + (int32_t)(grp * 32);
+            const int32_t u = v0 + (int32_t)lane;
+            const bool valid = u < p.v_hi;
+            // lanes past the bucket hold empty rows at its end
+            const int32_t a = __ldg(p.row_ptr + min(u, p.v_hi));
+            const int32_t e = __ldg(p.row_ptr + min(u + 1, p.v_hi));
+            const int32_t g = valid ? __ldg(p.gid + u) : -1;
+            // the group's first vertex decides the warp's histogram graph (a group spans at
+            // most a graph boundary or two; the other graph's entries go to global memory)
+            const int32_t g0 = __shfl_sync(0xffffffffu, g, 0);
+            if (g0 != warp_g) {
+                flush_hist(p, hw, warp_g, lane);
+                warp_g = g0;
+            }
+            const int32_t x_lo = __shfl_sync(0xffffffffu, a, 0), x_hi = __shfl_sync(0xffffffffu, e, 31);
+            unsigned long long lo = 0ull;
+            uint32_t hi = 0u;
+            for (int32_t x0 = x_lo; x0 < x_hi; x0 += 32) {
+                const int32_t x = x0 + (int32_t)lane;
+                const bool live = x < x_hi;
+                // row of entry x: the number of rows (lanes) ending at or before x
+                int r = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int32_t er = __shfl_sync(0xffffffffu, e, r + step - 1);
+                    if (er <= x) r += step;
+                }
+                const int32_t ur = v0 + r;
+                const int32_t v = live ? __ldg(p.col + x) : ur;
+                const uint32_t c = and_popc<W>(pull_row<W>(p, ur), pull_row<W>(p, v));
+                unsigned long long V = (v != ur) ? tabV[c] : 0ull;
+                const int32_t gr = __shfl_sync(0xffffffffu, g, r);
+                if (v > ur) {
+                    if (gr == warp_g) atomicAdd(hw + c, 1u);
+                    else atomicAdd(p.hist + __ldg(p.hoff + gr) + c, 1ull);
+                }
+                // inclusive scan of the 32 estimates (each below 2^57, so no step overflows)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, V, o);
+                    if ((int)lane >= o) V += y;
+                }
+                // this lane's row: entries [first, last] of the step
+                const int first = max(a, x0) - x0, last = min(e, x0 + 32) - x0 - 1;
+                const unsigned long long s_hi = __shfl_sync(0xffffffffu, V, min(max(last, 0), 31));
+                const unsigned long long s_lo = __shfl_sync(0xffffffffu, V, min(max(first - 1, 0), 31));
+                if (first <= last) acc_add(lo, hi, s_hi - (first > 0 ? s_lo : 0ull));
+            }
+            if (valid) {
+                const int32_t d = e - a;
+                double S, half;
+                if (hi == 0u) {
+                    S = fixed_to_f64(lo, kFixBits);
+                    half = fixed_to_f64(lo, kFixBits + 1);
+                } else {  // sums of 2^22 or more (double arithmetic, rare)
+                    S = (double)hi * 0x1p22 + (double)lo * 0x1p-42;
+                    half = 0.5 * S;
+                }
+                p.lcc[u] = d >= 2 ? (float)S / ((float)d * (float)(d - 1)) : 0.0f;
+                if (p.tri) p.tri[u] = half;
+            }
+        }
+    }
+    flush_hist(p, hw, warp_g, lane);
+}
+
+template <int W>
+cudaError_t run_pull(const PullParams &p, cudaStream_t s) {
+    const size_t smem = 8 * (size_t)(p.l + 1) + 4 * (size_t)(p.l + 1) * kPullWarps;
+    auto kern = k_batch_pull<W>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPullThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<per_sm * device_info().sm_count, kPullThreads, smem, s>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Variant v of the pull pass: v consecutive 32-vertex groups per warp chunk
+// (the autotuner's candidates below; a caller may set any v up to
+// kMaxPullVariant).
+constexpr int32_t kPullVariants[] = {1, 4, 16};
+constexpr int32_t kMaxPullVariant = 1024;
 
 __global__ void k_graph_ids(const int32_t *__restrict__ voff, int32_t graphs, int32_t *__restrict__ gid) {
     // one block per graph writes its vertex range
@@ -51,7 +259,6 @@ struct pg_batch {
     pg_csr g;
     int32_t graphs;
     uint32_t seed;
-    void *index;
     int32_t *gid;
     int32_t *voff;
     int64_t *hoff;
@@ -59,7 +266,6 @@ struct pg_batch {
     uint8_t *b_of;
     uint64_t *hist;
     int64_t hist_bins;
-    double *S;
     int32_t *hub;
     pg_tc_result *tc_out;
     float *lcc_out;
@@ -101,9 +307,9 @@ uint32_t budget_bits_pow2(double s, int64_t n, int64_t nnz) {
     return l;
 }
 
-// Carve the workspace (base == nullptr: only size it). Order: edge index,
-// graph tables, histograms, per-vertex sums, build scratch, then per bucket
-// its estimator table and sketch rows.
+// Carve the workspace (base == nullptr: only size it). Order: graph tables,
+// histograms, build scratch, then per bucket its estimator table and sketch
+// rows.
 size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, std::vector<Bucket> &buckets,
                    uint8_t *base, pg_batch *out) {
     size_t off = 0;
@@ -114,14 +320,12 @@ size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, 
     };
     int64_t bins = 0;
     for (int32_t i = 0; i < graphs; ++i) bins += (int64_t)cfg[i].bits + 1;
-    uint8_t *index = take(upper_index_bytes(g->n, g->nnz));
     uint8_t *gid = take(4 * (size_t)g->n + 4);
     uint8_t *voff = take(4 * ((size_t)graphs + 1));
     uint8_t *hoff = take(8 * ((size_t)graphs + 1));
     uint8_t *bits = take(4 * (size_t)graphs + 4);
     uint8_t *b = take((size_t)graphs + 4);
     uint8_t *hist = take(8 * (size_t)bins + 8);
-    uint8_t *S = take(8 * (size_t)g->n + 8);
     uint8_t *hub = take(build_workspace_bytes(g->nnz));
     for (Bucket &bk : buckets) {
         uint8_t *table = take(intersect_table_bytes(PG_SK_BLOOM, bk.bits, 0));
@@ -132,7 +336,6 @@ size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, 
         }
     }
     if (base && out) {
-        out->index = index;
         out->gid = reinterpret_cast<int32_t *>(gid);
         out->voff = reinterpret_cast<int32_t *>(voff);
         out->hoff = reinterpret_cast<int64_t *>(hoff);
@@ -140,7 +343,6 @@ size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, 
         out->b_of = b;
         out->hist = reinterpret_cast<uint64_t *>(hist);
         out->hist_bins = bins;
-        out->S = reinterpret_cast<double *>(S);
         out->hub = reinterpret_cast<int32_t *>(hub);
     }
     return off;
@@ -155,6 +357,8 @@ pg_status make_buckets(int32_t graphs, const int32_t *voff_host, const pg_batch_
         PG_REQUIRE(bits == 64 || bits == 128 || bits == 256 || bits == 512 || bits == 1024, PG_ERR_UNSUPPORTED,
                    "graph %d: batch Bloom bits %u not in {64, 128, 256, 512, 1024}", i, bits);
         PG_REQUIRE(b >= 1 && b <= 16, PG_ERR_INVALID_ARG, "graph %d: b = %u not in [1, 16]", i, b);
+        PG_REQUIRE(cfg[i].variant >= 0 && cfg[i].variant <= kMaxPullVariant, PG_ERR_INVALID_ARG,
+                   "graph %d: variant %d not in [0, %d]", i, cfg[i].variant, kMaxPullVariant);
         PG_REQUIRE(voff_host[i + 1] >= voff_host[i], PG_ERR_INVALID_ARG, "voff not non-decreasing at %d", i);
         if (!out.empty() && out.back().bits == bits && out.back().b == b) {
             out.back().g_hi = i + 1;
@@ -178,22 +382,7 @@ pg_status make_buckets(int32_t graphs, const int32_t *voff_host, const pg_batch_
     return PG_OK;
 }
 
-pg_sketch bucket_sketch(const pg_batch *bt, const Bucket &bk) {
-    pg_sketch sk{};
-    sk.kind = PG_SK_BLOOM;
-    sk.bits = bk.bits;
-    sk.b = bk.b;
-    sk.seed = bt->seed;
-    sk.n = bt->g.n;
-    sk.stride_bytes = bk.stride;
-    // rows are addressed by global vertex id; the bucket's rows start at v_lo
-    sk.data = bk.data - (int64_t)bk.v_lo * bk.stride;
-    return sk;
-}
-
 pg_status enqueue_builds(pg_batch *bt, cudaStream_t s) {
-    PG_TRY_CUDA(launch_upper_index(bt->g.row_ptr, bt->g.col, bt->g.n, bt->g.nnz, bt->index, s),
-                "pg_batch: edge index");
     for (const Bucket &bk : bt->buckets) {
         if (bk.v_hi <= bk.v_lo) continue;
         BatchMap bm{bt->gid, bt->voff, bt->b_of, bk.v_lo};
@@ -204,19 +393,48 @@ pg_status enqueue_builds(pg_batch *bt, cudaStream_t s) {
     return PG_OK;
 }
 
-pg_status enqueue_passes(pg_batch *bt, cudaStream_t s) {
-    launch_fill_u64(bt->hist, (size_t)bt->hist_bins, 0, s);
-    double *S = bt->S;
-    launch_fill_f64(S, (size_t)bt->g.n, 0.0, s);
-    const EdgeIndex ix = edge_index_view(bt->index, bt->g.n, bt->g.nnz);
+cudaError_t launch_pull(const pg_batch *bt, const Bucket &bk, int32_t variant, cudaStream_t s) {
+    PullParams p{};
+    p.row_ptr = bt->g.row_ptr;
+    p.col = bt->g.col;
+    p.v_lo = bk.v_lo;
+    p.v_hi = bk.v_hi;
+    p.data = bk.data - (int64_t)bk.v_lo * bk.stride;
+    p.stride = bk.stride;
+    p.l = bk.bits;
+    p.tabV = reinterpret_cast<const unsigned long long *>(bk.table + (bk.bits + 1));
+    p.gid = bt->gid;
+    p.hoff = bt->hoff;
+    p.hist = reinterpret_cast<unsigned long long *>(bt->hist);
+    p.lcc = bt->lcc_out;
+    p.tri = bt->tri_out;
+    p.chunk = variant;
+    switch (bk.bits) {
+        case 64: return run_pull<2>(p, s);
+        case 128: return run_pull<4>(p, s);
+        case 256: return run_pull<8>(p, s);
+        case 512: return run_pull<16>(p, s);
+        case 1024: return run_pull<32>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// The estimator table of every bucket (double | fixed point | float by popcount).
+pg_status enqueue_tables(pg_batch *bt, cudaStream_t s) {
     for (const Bucket &bk : bt->buckets) {
         if (bk.v_hi <= bk.v_lo) continue;
-        const pg_sketch sk = bucket_sketch(bt, bk);
-        PG_TRY_CUDA(launch_batch_pass(bt->g.row_ptr, bt->g.col, bt->g.n, ix, sk, PG_EST_BF_AND, bk.variant,
-                                      bt->gid, bt->hoff, bk.v_lo, bk.v_hi, bt->hist, S, bk.table, s),
-                    "pg_batch: pass");
+        PG_TRY_CUDA(launch_estimator_table(bk.table, PG_SK_BLOOM, PG_EST_BF_AND, bk.bits, bk.b, 0, s),
+                    "pg_batch: estimator table");
     }
-    PG_TRY_CUDA(launch_lcc_finalize(bt->g.row_ptr, bt->g.n, S, bt->lcc_out, bt->tri_out, s), "pg_batch: LCC");
+    return PG_OK;
+}
+
+pg_status enqueue_passes(pg_batch *bt, cudaStream_t s) {
+    launch_fill_u64(bt->hist, (size_t)bt->hist_bins, 0, s);
+    for (const Bucket &bk : bt->buckets) {
+        if (bk.v_hi <= bk.v_lo) continue;
+        PG_TRY_CUDA(launch_pull(bt, bk, bk.variant, s), "pg_batch: pass");
+    }
     PG_TRY_CUDA(launch_batch_finalize(bt->hist, bt->hoff, bt->bits_of, bt->b_of, bt->graphs, PG_EST_BF_AND,
                                       bt->tc_out, s),
                 "pg_batch: TC");
@@ -317,8 +535,14 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
         delete bt;
         return cuda_status(e, "pg_batch_create");
     }
-    // Autotune the lane mapping of every bucket whose variant is 0: build once,
-    // time each candidate pass on the bucket and keep the fastest.
+    // The estimator tables depend only on (l, b): computed once here.
+    st = enqueue_tables(bt, s);
+    if (st) {
+        delete bt;
+        return st;
+    }
+    // Autotune the lane/warp split of every bucket whose variant is 0: build
+    // once, time each candidate pass on the bucket and keep the fastest.
     bool tune = false;
     for (const Bucket &bk : bt->buckets) tune |= bk.variant == 0;
     if (tune) {
@@ -327,23 +551,18 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
             delete bt;
             return st;
         }
-        const EdgeIndex ix = edge_index_view(bt->index, g->n, g->nnz);
         cudaEvent_t a, b;
         cudaEventCreate(&a);
         cudaEventCreate(&b);
         for (size_t bi = 0; bi < bt->buckets.size(); ++bi) {
             Bucket &bk = bt->buckets[bi];
             if (bk.variant != 0) continue;
-            int32_t cand[4];
-            const int32_t nc = batch_variants(bk.bits, cand);
             float best = 1e30f;
-            int32_t best_v = cand[0];
-            const pg_sketch sk = bucket_sketch(bt, bk);
-            for (int32_t c = 0; c < nc; ++c) {
+            int32_t best_v = kPullVariants[0];
+            for (int32_t cand : kPullVariants) {
                 for (int rep = 0; rep < 2; ++rep) {  // first run warms up
                     cudaEventRecord(a, s);
-                    e = launch_batch_pass(g->row_ptr, g->col, g->n, ix, sk, PG_EST_BF_AND, cand[c], bt->gid,
-                                          bt->hoff, bk.v_lo, bk.v_hi, bt->hist, bt->S, bk.table, s);
+                    e = launch_pull(bt, bk, cand, s);
                     cudaEventRecord(b, s);
                     if (e == cudaSuccess) e = cudaEventSynchronize(b);
                     if (e != cudaSuccess) break;
@@ -351,7 +570,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
                     cudaEventElapsedTime(&ms, a, b);
                     if (rep == 1 && ms < best) {
                         best = ms;
-                        best_v = cand[c];
+                        best_v = cand;
                     }
                 }
                 if (e != cudaSuccess) break;

@@ -85,6 +85,22 @@ __device__ __forceinline__ uint32_t bit_pos(uint32_t h, uint32_t l) { return __u
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
+// Per-vertex sums avoid double-precision arithmetic on the hot path (double
+// throughput is a small fraction of the integer and float pipes on this GPU):
+// an estimate is carried as the exact integer V = round(value * 2^kFixBits)
+// (the uint64 column of the estimator tables), summed with integer adds, and
+// turned into a double by integer bit manipulation.
+constexpr int kFixBits = 42;
+// x * 2^-frac as a double, truncated to 53 significant bits (within 2^-52
+// relative); no floating-point instruction.
+__device__ __forceinline__ double fixed_to_f64(unsigned long long x, int frac) {
+    if (x == 0ull) return 0.0;
+    const int e = 63 - __clzll((long long)x);  // position of the leading one
+    const unsigned long long mant = e >= 52 ? (x >> (e - 52)) : (x << (52 - e));
+    const unsigned long long bits = ((unsigned long long)(e - frac + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+
 // ------------------------------------------------------------ launchers
 // Defined in pg_index.cu
 void launch_fill_u64(uint64_t *p, size_t count, uint64_t value, cudaStream_t s);
@@ -154,14 +170,6 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
                                 double *table_ws, cudaStream_t s);
 cudaError_t launch_tc_finalize(const uint64_t *hist, const pg_sketch &sk, int32_t estimator,
                                pg_tc_result *out, cudaStream_t s);
-// Batch (pg_batch.cu): the Bloom pass over the upper edges of vertices
-// [v_lo, v_hi) of a block-diagonal union graph, with per-graph histograms at
-// hist + hoff[gid[u]]; variant = lanes per row (batch_variants lists them).
-cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_t n, const EdgeIndex &ix,
-                              const pg_sketch &sk, int32_t estimator, int32_t variant, const int32_t *gid,
-                              const int64_t *hoff, int32_t v_lo, int32_t v_hi, uint64_t *hist, double *S,
-                              double *table_ws, cudaStream_t s);
-int32_t batch_variants(uint32_t bits, int32_t *out);
 // The estimator table of (kind, estimator, l, b, k) into table_ws
 // (intersect_table_bytes): double [len] | uint64 fixed point [len] | float [len],
 // indexed by the integer count (k-Hash: c / (k + c), scaled by d_u + d_v by the user).

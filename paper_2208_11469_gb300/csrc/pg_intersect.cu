@@ -41,9 +41,6 @@ struct Params {
     int64_t cap;            // list capacity
     const int32_t *pairs;   // pair list (pair source)
     int64_t P;
-    const int32_t *gid;     // batch: graph of each vertex (null: single graph)
-    const int64_t *hoff;    // batch: offset of each graph's histogram in hist
-    int32_t v_lo, v_hi;     // batch: this launch covers the upper edges of vertices [v_lo, v_hi)
     const uint8_t *data;
     int64_t stride;
     int32_t nvec;       // 16-byte vectors per row that carry payload
@@ -67,22 +64,7 @@ struct Params {
     int32_t want_union; // Bloom OR estimator: also count popcount(row_u OR row_v) (upper 16 bits)
 };
 
-// Per-vertex sums and per-edge estimates avoid double-precision arithmetic
-// on the hot path (double throughput is a small fraction of the integer and
-// float pipes on this GPU): an estimate is carried as the exact integer
-// V = round(value * 2^42) (kFixBits), summed with integer adds, and turned
-// into a double for the atomic by integer bit manipulation (truncating, so
-// within 2^-52 relative).
-constexpr int kFixBits = 42;
-
-__device__ __forceinline__ double fx_to_f64(unsigned long long x) {
-    if (x == 0ull) return 0.0;
-    const int e = 63 - __clzll((long long)x);  // position of the leading one
-    const unsigned long long mant = e >= 52 ? (x >> (e - 52)) : (x << (52 - e));
-    const unsigned long long bits =
-        ((unsigned long long)(e - kFixBits + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-}
+__device__ __forceinline__ double fx_to_f64(unsigned long long x) { return fixed_to_f64(x, kFixBits); }
 
 __device__ __forceinline__ uint4 ldg4(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
@@ -161,11 +143,6 @@ __device__ __forceinline__ void warp_range(const Params &p, int64_t &w0, int64_t
     int64_t lo = 0, hi;
     if (PAIRS) {
         hi = p.P;
-    } else if (p.gid) {
-        lo = p.upper_off[p.v_lo];
-        hi = p.upper_off[p.v_hi];
-        if (lo > p.cap) lo = p.cap;
-        if (hi > p.cap) hi = p.cap;
     } else {
         hi = p.upper_off[p.n];
         if (hi > p.cap) hi = p.cap;
@@ -437,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
 // The row of u stays in registers while u repeats (u is non-decreasing along
 // the list); the epilogue is the same as in k_pass, run by every lane for its
 // own item.
-template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool BATCH>
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
 __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     // W: 32-bit words of the row payload (l / 32 for Bloom, k for k-Hash)
     constexpr int NV = (W + 3) / 4;  // vectors per row
@@ -451,7 +428,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const int hk = (int)p.k + 1;
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * hk;
     const bool want_hist = p.hist != nullptr;
-    constexpr bool batch = BATCH;  // per-graph histograms of a batch bucket (p.gid, p.hoff)
     {
         const unsigned long long *gV = reinterpret_cast<const unsigned long long *>(p.table + p.table_len);
         const float *gF = reinterpret_cast<const float *>(p.table + 2 * p.table_len);
@@ -461,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             tabF[i] = gF[i];
         }
     }
-    if (want_hist && !batch)
+    if (want_hist)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
     __syncthreads();
 
@@ -476,9 +452,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const uint32_t grp_shift = (uint32_t)grp * 16u;
     const bool need_deg = p.need_deg != 0;
     const uint8_t *rowbase = p.data + 16 * vidx;
-    // sketch rows this launch may read: a batch launch holds only its bucket's rows
-    const int32_t row_lo = batch ? p.v_lo : 0;
-    const int32_t row_hi = batch ? p.v_hi - 1 : 0;
 
     int64_t w0, w1;
     warp_range<false>(p, w0, w1);
@@ -502,15 +475,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             for (int t = 0; t < SB; ++t) {
                 const unsigned src = (unsigned)(grp * L + s0 + t);  // lane owning this step's item
                 us[t] = __shfl_sync(0xffffffffu, cu, src);
-                // rows outside [row_lo, row_hi] (past the range, or a batch graph naming another
-                // graph's vertex) read a row of this launch's sketch table and count nothing useful
-                const int32_t vs_ = max(__shfl_sync(0xffffffffu, cv, src), row_lo);
-                const int32_t vt = batch ? min(vs_, row_hi) : vs_;
-                rb[t] = ldg4(rowbase + (int64_t)vt * p.stride);
+                // items past the range read row 0 and count nothing
+                const int32_t vs_ = max(__shfl_sync(0xffffffffu, cv, src), 0);
+                rb[t] = ldg4(rowbase + (int64_t)vs_ * p.stride);
                 if (UREUSE && us[t] == cur_u)
                     ra[t] = cur_row;
                 else
-                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], row_lo) * p.stride);
+                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], 0) * p.stride);
             }
 #pragma unroll
             for (int t = 0; t < SB; ++t) {
@@ -551,7 +522,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
                     est_d = tab[c];
                     est_f = tabF[c];
                 }
-                if (want_hist && !batch) atomicAdd(h32 + c, 1u);
+                if (want_hist) atomicAdd(h32 + c, 1u);
             } else {
                 const uint32_t ds = (uint32_t)cdu + (uint32_t)cdv;
                 if (p.need_est) {
@@ -572,22 +543,13 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             if (p.S) atomicAdd(p.S + cv, est_d);
         }
         if (p.S) add_u_runs(p.S, cu, V);
-        if (batch && want_hist) {
-            // per-graph histograms in global memory; lanes with the same (graph, count) add once
-            const int32_t gg = cu >= 0 ? __ldg(p.gid + cu) : -1;
-            const uint32_t key = cu >= 0 ? (uint32_t)gg * 2048u + c : 0xFFFFFFFFu;
-            const unsigned same = __match_any_sync(0xffffffffu, key);
-            if (cu >= 0 && (int)lane == __ffs(same) - 1)
-                atomicAdd(reinterpret_cast<unsigned long long *>(p.hist + __ldg(p.hoff + gg) + c),
-                          (unsigned long long)__popc(same));
-        }
         cu = nu;
         cv = nv;
         cdu = ndu;
         cdv = ndv;
     }
 
-    if (want_hist && !batch) {
+    if (want_hist) {
         __syncthreads();
         if (KIND == BLOOM) {
             for (int i = threadIdx.x; i < h32_len; i += blockDim.x)
@@ -935,11 +897,11 @@ cudaError_t run_pass(const Params &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool BATCH = false>
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
 cudaError_t run_lean(const Params &p, cudaStream_t s) {
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
     const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)h32_len : 0);
-    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB, BATCH>;
+    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1068,66 +1030,11 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     }
 }
 
-cudaError_t launch_batch_pass(const int32_t *row_ptr, const int32_t *col, int32_t n, const EdgeIndex &ix,
-                              const pg_sketch &sk, int32_t estimator, int32_t variant, const int32_t *gid,
-                              const int64_t *hoff, int32_t v_lo, int32_t v_hi, uint64_t *hist, double *S,
-                              double *table_ws, cudaStream_t s) {
-    Params p{};
-    p.row_ptr = row_ptr;
-    p.col = col;
-    p.n = n;
-    p.upper_off = ix.upper_off;
-    p.eu = ix.eu;
-    p.ev = ix.ev;
-    p.edu = ix.edu;
-    p.edv = ix.edv;
-    p.cap = ix.cap;
-    p.data = static_cast<const uint8_t *>(sk.data);
-    p.stride = sk.stride_bytes;
-    p.l = sk.bits;
-    p.k = sk.k;
-    p.est = estimator;
-    p.S = S;
-    p.hist = hist;
-    p.hist_len = (int32_t)hist_bins(sk.kind, sk.bits, sk.k, estimator);
-    p.table = table_ws;
-    p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
-    p.need_est = S ? 1 : 0;
-    p.need_deg = 0;
-    p.gid = gid;
-    p.hoff = hoff;
-    p.v_lo = v_lo;
-    p.v_hi = v_hi;
-    p.nvec = (int32_t)(sk.bits / 128 + ((sk.bits % 128) ? 1 : 0));
-    k_table<<<1, 256, 0, s>>>(table_ws, p.table_len, sk.kind, estimator, sk.bits, sk.b, sk.k);
-    note_launch();
-    // variant: lanes per row (the autotuner times the candidates of each width)
-    switch (sk.bits) {
-        case 64: return variant == 2 ? run_lean<BLOOM, 2, 2, 2, true, 3, true>(p, s) : run_lean<BLOOM, 1, 2, 1, true, 4, true>(p, s);
-        case 128: return variant == 2 ? run_lean<BLOOM, 2, 4, 2, true, 3, true>(p, s) : run_lean<BLOOM, 1, 4, 1, true, 4, true>(p, s);
-        case 256: return variant == 4 ? run_lean<BLOOM, 4, 8, 4, true, 3, true>(p, s) : run_lean<BLOOM, 2, 8, 2, true, 3, true>(p, s);
-        case 512: return variant == 8 ? run_lean<BLOOM, 8, 16, 2, true, 3, true>(p, s) : run_lean<BLOOM, 4, 16, 4, true, 3, true>(p, s);
-        case 1024: return run_lean<BLOOM, 8, 32, 2, true, 3, true>(p, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 cudaError_t launch_estimator_table(double *table_ws, int32_t kind, int32_t estimator, uint32_t l, uint32_t b,
                                    uint32_t k, cudaStream_t s) {
     k_table<<<1, 256, 0, s>>>(table_ws, (int32_t)table_len(kind, l, k), kind, estimator, l, b, k);
     note_launch();
     return cudaGetLastError();
-}
-
-int32_t batch_variants(uint32_t bits, int32_t *out) {
-    switch (bits) {
-        case 64: out[0] = 1; out[1] = 2; return 2;
-        case 128: out[0] = 1; out[1] = 2; return 2;
-        case 256: out[0] = 2; out[1] = 4; return 2;
-        case 512: out[0] = 4; out[1] = 8; return 2;
-        case 1024: out[0] = 8; return 1;
-        default: return 0;
-    }
 }
 
 cudaError_t launch_batch_finalize(const uint64_t *hist, const int64_t *hoff, const uint32_t *bits_of,

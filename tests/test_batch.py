@@ -81,6 +81,9 @@ def test_workspace_rejects_bad_batches(pg):
     assert ws([(256, 2), (300, 2), (300, 2)]) == 0
     assert "300" in L.pg_last_error().decode()
     assert ws([(256, 0), (256, 0), (256, 0)]) == 0
+    arr = (pg.BatchConfig * 3)(*[pg.BatchConfig(256, 2, v, 0) for v in (1, 1025, 1)])
+    assert L.pg_batch_workspace_bytes(ctypes.byref(c), 3, voff.ctypes.data_as(ctypes.c_void_p), arr) == 0
+    assert "variant" in L.pg_last_error().decode()
     bad = np.array([0, 20, 10, 30], dtype=np.int32)
     arr = (pg.BatchConfig * 3)(*[pg.BatchConfig(256, 2, 0, 0)] * 3)
     assert L.pg_batch_workspace_bytes(ctypes.byref(c), 3, bad.ctypes.data_as(ctypes.c_void_p), arr) == 0
@@ -171,7 +174,7 @@ def test_batch_matches_single_graph_calls(pg):
         # per-vertex triangles sum to three times each graph's estimate
         for i in range(len(parts)):
             assert tri[voff[i]:voff[i + 1]].sum() == pytest.approx(3 * got[i]["est_tc"], rel=1e-9, abs=1e-9)
-    assert all(v in (1, 2, 4, 8) for v in batch.variants)
+    assert all(v in (1, 4, 16) for v in batch.variants)
     batch.close()
 
 
@@ -198,18 +201,24 @@ def test_batch_against_oracle(pg):
 
 
 @pytest.mark.gpu
-def test_batch_variants_give_identical_integers(pg):
-    """Every lane mapping of a width computes the same counts: fix each
-    candidate in turn and compare the integer totals."""
+def test_batch_variants_give_identical_results(pg):
+    """The per-vertex sums are exact fixed-point sums, so every work mapping
+    (variant = 32-vertex groups per warp chunk) gives bit-identical per-graph
+    totals, LCC and per-vertex triangles, and so do repeated runs."""
     parts = synth.batch_mix(6, seed=21, log2_n=(9, 12))
     rp, cl, voff = synth.block_diagonal(parts)
     g = pg.graph(rp.cuda(), cl.cuda(), build_index=False)
-    for bits, variants in ((64, (1, 2)), (128, (1, 2)), (256, (2, 4)), (512, (4, 8))):
+    for bits in (64, 128, 256, 512, 1024):
         res = []
-        for var in variants:
-            bt = pg.Batch(g, voff, [(bits, 2, var)] * len(parts), seed=1)
+        for var in (1, 3, 16, 1):
+            bt = pg.Batch(g, voff, [(bits, 2, var)] * len(parts), seed=1, want_tri=True)
             bt.run()
-            res.append([(r["edges"], r["count_sum"]) for r in bt.results()])
+            torch.cuda.synchronize()
+            res.append(([(r["edges"], r["count_sum"], r["est_tc"]) for r in bt.results()], bt.lcc.cpu().numpy(),
+                        bt.tri.cpu().numpy()))
             assert bt.variants == [var] * len(parts)
             bt.close()
-        assert res[0] == res[1], bits
+        for other in res[1:]:
+            assert other[0] == res[0][0], bits
+            np.testing.assert_array_equal(other[1], res[0][1])
+            np.testing.assert_array_equal(other[2], res[0][2])
