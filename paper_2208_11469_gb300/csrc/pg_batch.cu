@@ -230,6 +230,106 @@ cudaError_t run_pull(const PullParams &p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ Bloom build
+// The Bloom filters of a bucket's vertices, with the pull pass's work order
+// and walk: a warp takes 32 consecutive rows, builds their filters in its
+// shared memory (row r at [r * words, (r + 1) * words)) from the rows'
+// entries taken 32 at a time (coalesced loads, one entry per lane, its row
+// from the search over the row ends), and stores the 32 filters with one
+// coalesced row store per lane. Every graph hashes its own ids (global id
+// minus the graph's first id) with the bucket's b hash functions, so the
+// filter bits are those of the single-graph build (Sec. II-B: bit
+// floor(h_i(x) l / 2^32) for each element x and i < b); OR does not depend
+// on the order in which entries are hashed.
+struct BuildParams {
+    const int32_t *row_ptr;
+    const int32_t *col;
+    int32_t v_lo, v_hi;
+    const int32_t *gid;
+    const int32_t *voff;
+    uint8_t *data;       // rows addressed by global vertex id
+    int64_t stride;
+    uint32_t l, b, seed;
+    int32_t chunk;
+};
+
+template <int WORDS>  // 32-bit words per stored row (stride / 4)
+__global__ void __launch_bounds__(kPullThreads) k_batch_bloom(BuildParams p) {
+    __shared__ uint32_t filt[kPullWarps][32 * WORDS];
+    __shared__ uint32_t pre_s[16];
+    if (threadIdx.x < 16) pre_s[threadIdx.x] = fmix_pre(hash_seed(p.seed, threadIdx.x));
+    const unsigned lane = lane_id();
+    uint32_t *f = filt[threadIdx.x >> 5];
+    for (int i = (int)lane; i < 32 * WORDS; i += 32) f[i] = 0u;
+    __syncthreads();
+    const int64_t warp = ((int64_t)blockIdx.x * kPullThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * kPullWarps;
+    const int64_t groups = ((int64_t)p.v_hi - p.v_lo + 31) / 32;
+    const int64_t chunks = (groups + p.chunk - 1) / p.chunk;
+    for (int64_t ch = warp; ch < chunks; ch += warps) {
+        for (int gi = 0; gi < p.chunk; ++gi) {
+            const int64_t grp = ch * p.chunk + gi;
+            if (grp >= groups) break;
+            const int32_t v0 = p.v_lo + (int32_t)(grp * 32);
+            const int32_t u = v0 + (int32_t)lane;
+            const bool valid = u < p.v_hi;
+            const int32_t a = __ldg(p.row_ptr + min(u, p.v_hi));
+            const int32_t e = __ldg(p.row_ptr + min(u + 1, p.v_hi));
+            const int32_t id0 = valid ? __ldg(p.voff + __ldg(p.gid + u)) : 0;
+            const int32_t x_lo = __shfl_sync(0xffffffffu, a, 0), x_hi = __shfl_sync(0xffffffffu, e, 31);
+            for (int32_t x0 = x_lo; x0 < x_hi; x0 += 32) {
+                const int32_t x = x0 + (int32_t)lane;
+                int r = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int32_t er = __shfl_sync(0xffffffffu, e, r + step - 1);
+                    if (er <= x) r += step;
+                }
+                const int32_t idr = __shfl_sync(0xffffffffu, id0, r);
+                if (x < x_hi) {
+                    const uint32_t px = fmix_pre((uint32_t)(__ldg(p.col + x) - idr));
+                    uint32_t *fr = f + r * WORDS;
+                    for (uint32_t i = 0; i < p.b; ++i) {
+                        const uint32_t q = bit_pos(hash_pre(px, pre_s[i]), p.l);
+                        atomicOr(fr + (q >> 5), 1u << (q & 31u));
+                    }
+                }
+            }
+            __syncwarp();
+            // lane r stores row r (padding words stay zero) and clears it
+            uint32_t *fr = f + lane * WORDS;
+            if (valid) {
+                uint4 *dst = reinterpret_cast<uint4 *>(p.data + (int64_t)u * p.stride);
+#pragma unroll
+                for (int q = 0; q < WORDS / 4; ++q)
+                    dst[q] = make_uint4(fr[4 * q], fr[4 * q + 1], fr[4 * q + 2], fr[4 * q + 3]);
+            }
+#pragma unroll
+            for (int w = 0; w < WORDS; ++w) fr[w] = 0u;
+            __syncwarp();
+        }
+    }
+}
+
+template <int WORDS>
+cudaError_t run_batch_bloom(const BuildParams &p, cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bloom<WORDS>, kPullThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    k_batch_bloom<WORDS><<<per_sm * device_info().sm_count, kPullThreads, 0, s>>>(p);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// Groups of 32 rows per warp chunk of the build.
+constexpr int32_t kBuildChunk = 4;
+// Buckets of at most this many bits use k_batch_bloom; wider filters use the
+// single-graph builder (lane-private filters for short rows, hub rows split
+// across blocks), which was faster there: at 512 bits the few large graphs
+// of a bucket leave the flat walk too few groups and long rows to one warp.
+constexpr uint32_t kFlatBuildMaxBits = 64;
+
 // Variant v of the pull pass: v consecutive 32-vertex groups per warp chunk
 // (the autotuner's candidates below; a caller may set any v up to
 // kMaxPullVariant).
@@ -382,13 +482,40 @@ pg_status make_buckets(int32_t graphs, const int32_t *voff_host, const pg_batch_
     return PG_OK;
 }
 
+cudaError_t launch_batch_bloom(const pg_batch *bt, const Bucket &bk, cudaStream_t s) {
+    BuildParams p{};
+    p.row_ptr = bt->g.row_ptr;
+    p.col = bt->g.col;
+    p.v_lo = bk.v_lo;
+    p.v_hi = bk.v_hi;
+    p.gid = bt->gid;
+    p.voff = bt->voff;
+    p.data = bk.data - (int64_t)bk.v_lo * bk.stride;
+    p.stride = bk.stride;
+    p.l = bk.bits;
+    p.b = bk.b;
+    p.seed = bt->seed;
+    p.chunk = kBuildChunk;
+    switch (bk.stride / 4) {
+        case 4: return run_batch_bloom<4>(p, s);
+        case 8: return run_batch_bloom<8>(p, s);
+        case 16: return run_batch_bloom<16>(p, s);
+        case 32: return run_batch_bloom<32>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 pg_status enqueue_builds(pg_batch *bt, cudaStream_t s) {
     for (const Bucket &bk : bt->buckets) {
         if (bk.v_hi <= bk.v_lo) continue;
-        BatchMap bm{bt->gid, bt->voff, bt->b_of, bk.v_lo};
-        PG_TRY_CUDA(launch_build_bloom(bt->g.row_ptr + bk.v_lo, bt->g.col, bk.v_hi - bk.v_lo, bk.bits, bk.b,
-                                       bt->seed, bk.data, bk.stride, bt->hub, s, &bm),
-                    "pg_batch: Bloom build");
+        if (bk.bits <= kFlatBuildMaxBits) {
+            PG_TRY_CUDA(launch_batch_bloom(bt, bk, s), "pg_batch: Bloom build");
+        } else {
+            BatchMap bm{bt->gid, bt->voff, bt->b_of, bk.v_lo};
+            PG_TRY_CUDA(launch_build_bloom(bt->g.row_ptr + bk.v_lo, bt->g.col, bk.v_hi - bk.v_lo, bk.bits, bk.b,
+                                           bt->seed, bk.data, bk.stride, bt->hub, s, &bm),
+                        "pg_batch: Bloom build");
+        }
     }
     return PG_OK;
 }

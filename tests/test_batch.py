@@ -179,6 +179,34 @@ def test_batch_matches_single_graph_calls(pg):
 
 
 @pytest.mark.gpu
+def test_64_bit_build_with_hub_rows(pg):
+    """The 64-bit buckets use their own builder (one warp walks 32 rows'
+    entries, so a hub row is walked by one warp): a graph with a 9500-entry
+    hub row and graphs with isolated vertices give the single-graph results."""
+    n = 12000
+    rp, cl = synth.erdos_renyi(n, 6.0, seed=4)
+    src = torch.repeat_interleave(torch.arange(n), (rp[1:] - rp[:-1]).long())
+    hub = torch.randperm(n, generator=torch.Generator().manual_seed(2))[:9500]
+    u = torch.cat([src, torch.full((9500,), 77, dtype=torch.int64)])
+    v = torch.cat([cl.long(), hub])
+    parts = [synth.csr_from_pairs(u.long(), v.long(), n), synth.from_edges(40, [(0, 1), (1, 2), (0, 2)]),
+             synth.erdos_renyi(300, 4.0, seed=8)]
+    cfg = [(64, 2)] * len(parts)
+    rp_u, cl_u, voff = synth.block_diagonal(parts)
+    batch = pg.Batch(pg.graph(rp_u.cuda(), cl_u.cuda(), build_index=False), voff, cfg, seed=3)
+    batch.run()
+    torch.cuda.synchronize()
+    got = batch.results()
+    lcc = batch.lcc.cpu().numpy()
+    for i, (p_, c) in enumerate(zip(parts, cfg)):
+        w, wl = _single(pg, p_[0], p_[1], c[0], c[1], 3)
+        assert (got[i]["edges"], got[i]["count_sum"]) == (w["edges"], w["count_sum"]), i
+        assert got[i]["est_tc"] == pytest.approx(w["est_tc"], rel=RTOL_F64, abs=1e-12)
+        np.testing.assert_allclose(lcc[voff[i]:voff[i + 1]], wl, rtol=RTOL_F32, atol=1e-6)
+    batch.close()
+
+
+@pytest.mark.gpu
 def test_batch_against_oracle(pg):
     from oracle import oracle as O
     parts = synth.batch_mix(4, seed=3, log2_n=(7, 10))
