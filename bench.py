@@ -252,8 +252,18 @@ class Pipeline:
     def sketched_per_step(self) -> int:
         return self.m * len(self.passes)
 
-    def step(self, ev=None):
-        """One pass of the hot path. ev: optional dict name -> (start, end) events."""
+    def sketches(self):
+        """The distinct sketches of the step, in build order."""
+        out, seen = [], set()
+        for _, sk, _ in self.passes:
+            if id(sk) not in seen:
+                seen.add(id(sk))
+                out.append(sk)
+        return out
+
+    def step(self, ev=None, builds=True):
+        """One pass of the hot path. ev: optional dict name -> (start, end) events.
+        builds=False: the sketches are already built (by upload_build)."""
         pg, g = self.pg, self.g
         s = torch.cuda.current_stream()
 
@@ -264,7 +274,7 @@ class Pipeline:
         mark("index", 0)
         pg.build_edge_index_into(g)
         mark("index", 1)
-        built = set()
+        built = set() if builds else {id(sk) for _, sk, _ in self.passes}
         for name, sk, est in self.passes:
             if id(sk) in built:
                 continue
@@ -335,7 +345,10 @@ def time_steps(pipe: Pipeline, steps: int, warmup: int, ws: int):
 
 def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     """The same step through the public API from pinned host buffers: the CSR
-    copy host->device and the results device->host are inside the timing."""
+    copy host->device and the results device->host are inside the timing.
+    The upload goes through pg_upload_build, which copies the CSR in row
+    chunks and builds the sketches of each chunk while the next one is
+    copied; the edge index and the passes follow."""
     pg = pipe.pg
     g = pipe.g
     d2h = []
@@ -347,10 +360,10 @@ def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     t0 = time.perf_counter()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
+    sketches = pipe.sketches()
     for _ in range(steps):
-        g.row_ptr.copy_(host_rp, non_blocking=True)
-        g.col.copy_(host_col, non_blocking=True)
-        pipe.step()
+        pg.upload_build(g, host_rp, host_col, sketches, workspace=pipe.build_ws)
+        pipe.step(builds=False)
         for dev_t, host_t in d2h:
             host_t.copy_(dev_t, non_blocking=True)
     end.record()

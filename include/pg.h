@@ -170,6 +170,27 @@ pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *workspace,
 pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *workspace,
                            size_t workspace_bytes, pg_stream_t stream);
 
+/* Upload a CSR from HOST memory (page-locked for the copies to overlap) into
+ * the DEVICE CSR g and build sketches of its rows while it lands: row_ptr is
+ * copied first, then col in chunks of whole rows (about chunk_entries
+ * entries each, at least one row) on copy_stream; after each chunk, stream
+ * waits for it and builds every sketch's rows of that chunk (the builds of
+ * Sec. II-C are per row, so the result equals pg_build_bloom /
+ * pg_build_minhash on the uploaded CSR). The copies start after the work
+ * already enqueued on stream, so a previous step that reads g is not
+ * overwritten. When the call returns, stream is ordered after the whole
+ * upload and the builds; copy_stream may equal stream (no overlap).
+ * host_row_ptr: HOST int32 [n+1] from 0 to nnz, non-decreasing (it is read
+ * on the host to cut the chunks); host_col: HOST int32 [nnz]. sketches:
+ * HOST array of count descriptors (any kinds, DEVICE data for g's n rows);
+ * ws: DEVICE build workspace (pg_build_workspace_bytes), shared by the
+ * builds in stream order. Errors: PG_ERR_INVALID_ARG (NULLs, offsets not
+ * from 0 to nnz, sketch checks as for the builders), PG_ERR_NO_MEMORY
+ * (workspace too small), PG_ERR_CUDA. Asynchronous. */
+pg_status pg_upload_build(const int32_t *host_row_ptr, const int32_t *host_col, const pg_csr *g,
+                          const pg_sketch *sketches, int32_t count, void *workspace, size_t workspace_bytes,
+                          int64_t chunk_entries, pg_stream_t copy_stream, pg_stream_t stream);
+
 /* Sketch files (checkpoint / resume of the sketches, which are a pure
  * function of the CSR, the parameters and the seed): a 64-byte header
  * {"PGSKTCH1", version 1, kind, bits, b, k, seed, n, stride, n * stride}

@@ -299,6 +299,82 @@ pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *ws, size_
     return PG_OK;
 }
 
+pg_status pg_upload_build(const int32_t *host_row_ptr, const int32_t *host_col, const pg_csr *g,
+                          const pg_sketch *sketches, int32_t count, void *ws, size_t ws_bytes,
+                          int64_t chunk_entries, pg_stream_t copy_stream, pg_stream_t stream) {
+    PG_TRACE("pg_upload_build");
+    pg_status st = check_graph(g);
+    if (st) return st;
+    PG_REQUIRE(host_row_ptr != nullptr && (g->nnz == 0 || host_col != nullptr), PG_ERR_INVALID_ARG,
+               "pg_upload_build: host CSR is NULL");
+    PG_REQUIRE(count >= 0 && (count == 0 || sketches != nullptr), PG_ERR_INVALID_ARG,
+               "pg_upload_build: bad sketch list");
+    PG_REQUIRE(chunk_entries > 0, PG_ERR_INVALID_ARG, "pg_upload_build: chunk_entries must be positive");
+    PG_REQUIRE(host_row_ptr[0] == 0 && (int64_t)host_row_ptr[g->n] == g->nnz, PG_ERR_INVALID_ARG,
+               "pg_upload_build: host row_ptr must run from 0 to nnz");
+    for (int32_t i = 0; i < count; ++i) {
+        st = build_common(g, sketches + i, ws, ws_bytes);
+        if (st) return st;
+        PG_REQUIRE(sketches[i].kind == PG_SK_BLOOM || sketches[i].kind == PG_SK_KHASH ||
+                       sketches[i].kind == PG_SK_1HASH,
+                   PG_ERR_INVALID_ARG, "pg_upload_build: sketch %d has an unknown kind", i);
+    }
+    // the device CSR is this call's output (pg_csr holds it as const for the readers)
+    int32_t *dst_rp = const_cast<int32_t *>(g->row_ptr);
+    int32_t *dst_col = const_cast<int32_t *>(g->col);
+    cudaStream_t cs = copy_stream, s = stream;
+    cudaEvent_t ev_start = nullptr, ev_chunk = nullptr;
+    PG_TRY_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming), "pg_upload_build: event");
+    cudaError_t e = cudaEventCreateWithFlags(&ev_chunk, cudaEventDisableTiming);
+    // the upload overwrites the device CSR: it starts after the work already on the compute stream
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dst_rp, host_row_ptr, 4 * ((size_t)g->n + 1), cudaMemcpyDefault, cs);
+    int64_t copied = 0;  // col entries copied so far
+    int32_t r0 = 0;
+    while (e == cudaSuccess && (r0 < g->n || copied < g->nnz)) {
+        // rows [r0, r1): as many whole rows as fit chunk_entries (at least one)
+        int32_t r1 = g->n;
+        if (r0 < g->n) {
+            const int64_t target = (int64_t)host_row_ptr[r0] + chunk_entries;
+            const int32_t *it = std::upper_bound(host_row_ptr + r0 + 1, host_row_ptr + g->n + 1, target,
+                                                 [](int64_t t, int32_t x) { return t < (int64_t)x; });
+            r1 = std::max<int32_t>(r0 + 1, (int32_t)(it - host_row_ptr) - 1);
+            r1 = std::min<int32_t>(r1, g->n);
+        }
+        const int64_t end = std::min<int64_t>(g->nnz, std::max<int64_t>(copied, host_row_ptr[r1]));
+        if (end > copied)
+            e = cudaMemcpyAsync(dst_col + copied, host_col + copied, 4 * (size_t)(end - copied), cudaMemcpyDefault,
+                                cs);
+        copied = end;
+        if (r1 == g->n) copied = g->nnz;  // non-monotone offsets: the last chunk takes the rest
+        if (e == cudaSuccess && r1 == g->n && end < g->nnz)
+            e = cudaMemcpyAsync(dst_col + end, host_col + end, 4 * (size_t)(g->nnz - end), cudaMemcpyDefault, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_chunk, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_chunk, 0);
+        for (int32_t i = 0; e == cudaSuccess && i < count && r1 > r0; ++i) {
+            const pg_sketch &sk = sketches[i];
+            uint8_t *rows = static_cast<uint8_t *>(sk.data) + (int64_t)r0 * sk.stride_bytes;
+            int32_t *hub = static_cast<int32_t *>(ws);
+            if (sk.kind == PG_SK_BLOOM)
+                e = launch_build_bloom(g->row_ptr + r0, g->col, r1 - r0, sk.bits, sk.b, sk.seed, rows,
+                                       sk.stride_bytes, hub, s);
+            else if (sk.kind == PG_SK_KHASH)
+                e = launch_build_khash(g->row_ptr + r0, g->col, r1 - r0, sk.k, sk.seed, rows, sk.stride_bytes, hub,
+                                       s);
+            else
+                e = launch_build_1hash(g->row_ptr + r0, g->col, r1 - r0, sk.k, sk.seed, rows, sk.stride_bytes, hub,
+                                       s);
+        }
+        r0 = r1;
+    }
+    cudaEventDestroy(ev_start);
+    if (ev_chunk) cudaEventDestroy(ev_chunk);
+    PG_TRY_CUDA(e, "pg_upload_build");
+    return PG_OK;
+}
+
 int64_t pg_hist_bins(const pg_sketch *sk, int32_t estimator) {
     if (!sk || estimator == PG_EST_EXACT) return 0;
     return hist_bins(sk->kind, sk->bits, sk->k, estimator);

@@ -32,7 +32,7 @@ SYMBOLS = [
     "pg_status_string", "pg_last_error", "pg_version", "pg_validate_csr", "pg_edge_index_bytes",
     "pg_build_edge_index", "pg_edge_index_upper_off", "pg_sketch_stride",
     "pg_bloom_bits_for_budget", "pg_build_workspace_bytes", "pg_build_bloom", "pg_build_minhash",
-    "pg_sketch_save", "pg_sketch_load_header", "pg_sketch_load",
+    "pg_upload_build", "pg_sketch_save", "pg_sketch_load_header", "pg_sketch_load",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick", "pg_clique4_workspace_bytes", "pg_clique4_count",
@@ -151,6 +151,7 @@ def lib() -> ctypes.CDLL:
                 "pg_build_workspace_bytes": (sz, [P(Csr)]),
                 "pg_build_bloom": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
                 "pg_build_minhash": (i32, [P(Csr), P(SketchDesc), vp, sz, vp]),
+                "pg_upload_build": (i32, [vp, vp, P(Csr), P(SketchDesc), i32, vp, sz, i64, vp, vp]),
                 "pg_sketch_save": (i32, [P(SketchDesc), ctypes.c_char_p, vp]),
                 "pg_sketch_load_header": (i32, [ctypes.c_char_p, P(SketchDesc)]),
                 "pg_sketch_load": (i32, [P(SketchDesc), ctypes.c_char_p, vp]),
@@ -361,6 +362,34 @@ def build_minhash(g: Graph, kind: int, k: int, seed: int, stride: int | None = N
     _check(lib().pg_build_minhash(ctypes.byref(c), ctypes.byref(d), _ptr(ws), ws.numel(), _stream()),
            "pg_build_minhash")
     return sk
+
+
+def upload_build(g: Graph, host_row_ptr: torch.Tensor, host_col: torch.Tensor, sketches, *,
+                 workspace: torch.Tensor | None = None, chunk_entries: int | None = None, copy_stream=None):
+    """pg_upload_build: copy the CSR from host tensors (page-locked for overlap)
+    into g's device buffers in row chunks on copy_stream (a torch.cuda.Stream;
+    None: a stream of this module) while the current stream builds every
+    sketch's rows of each chunk as it lands. The sketches must be allocated
+    for g (alloc_sketch) and carry their kind and parameters."""
+    assert host_row_ptr.device.type == "cpu" and host_col.device.type == "cpu"
+    assert host_row_ptr.dtype == torch.int32 and host_col.dtype == torch.int32
+    assert host_row_ptr.is_contiguous() and host_col.is_contiguous()
+    ws = workspace if workspace is not None else _dev_bytes(build_workspace_bytes(g), g.device)
+    if chunk_entries is None:
+        chunk_entries = max(1 << 20, g.nnz // 8)
+    if copy_stream is None:
+        global _upload_stream
+        if _upload_stream is None:
+            _upload_stream = torch.cuda.Stream(device=g.device)
+        copy_stream = _upload_stream
+    descs = (SketchDesc * max(len(sketches), 1))(*[sk.desc() for sk in sketches])
+    c = g.csr()
+    _check(lib().pg_upload_build(host_row_ptr.data_ptr(), host_col.data_ptr(), ctypes.byref(c), descs,
+                                 len(sketches), _ptr(ws), ws.numel(), int(chunk_entries),
+                                 copy_stream.cuda_stream, _stream()), "pg_upload_build")
+
+
+_upload_stream = None
 
 
 # ----------------------------------------------------------------- analysis
