@@ -428,7 +428,8 @@ pg_status pg_batch_autotune(const int32_t *n, const int64_t *nnz, int32_t graphs
                             pg_batch_config *cfg);
 
 /* Device workspace a batch needs (graph tables, per-graph histograms,
- * estimator tables, sketches); 0 for invalid arguments. */
+ * estimator tables, sketches); 0 for invalid arguments, including a union
+ * graph of more than 2^31 - 65 CSR entries. */
 size_t pg_batch_workspace_bytes(const pg_csr *g, int32_t graphs, const int32_t *voff,
                                 const pg_batch_config *cfg);
 

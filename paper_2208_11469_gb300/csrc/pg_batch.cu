@@ -600,6 +600,11 @@ pg_status pg_batch_autotune(const int32_t *n_host, const int64_t *nnz_host, int3
 size_t pg_batch_workspace_bytes(const pg_csr *g, int32_t graphs, const int32_t *voff_host,
                                 const pg_batch_config *cfg_host) {
     if (!g || graphs < 1 || !voff_host || !cfg_host) return 0;
+    // the row walks step a 32-bit entry index by 32 past the last entry
+    if (g->nnz > (int64_t)INT32_MAX - 64) {
+        set_error(PG_ERR_TOO_LARGE, "pg_batch: nnz %lld above %d", (long long)g->nnz, INT32_MAX - 64);
+        return 0;
+    }
     std::vector<Bucket> buckets;
     if (make_buckets(graphs, voff_host, cfg_host, buckets) != PG_OK) return 0;
     return carve_batch(g, graphs, cfg_host, buckets, nullptr, nullptr);

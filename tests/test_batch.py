@@ -84,6 +84,10 @@ def test_workspace_rejects_bad_batches(pg):
     arr = (pg.BatchConfig * 3)(*[pg.BatchConfig(256, 2, v, 0) for v in (1, 1025, 1)])
     assert L.pg_batch_workspace_bytes(ctypes.byref(c), 3, voff.ctypes.data_as(ctypes.c_void_p), arr) == 0
     assert "variant" in L.pg_last_error().decode()
+    big = _csr_stub(30, 2**31 - 40)
+    arr = (pg.BatchConfig * 3)(*[pg.BatchConfig(256, 2, 0, 0)] * 3)
+    assert L.pg_batch_workspace_bytes(ctypes.byref(big), 3, voff.ctypes.data_as(ctypes.c_void_p), arr) == 0
+    assert "nnz" in L.pg_last_error().decode()
     bad = np.array([0, 20, 10, 30], dtype=np.int32)
     arr = (pg.BatchConfig * 3)(*[pg.BatchConfig(256, 2, 0, 0)] * 3)
     assert L.pg_batch_workspace_bytes(ctypes.byref(c), 3, bad.ctypes.data_as(ctypes.c_void_p), arr) == 0
