@@ -453,6 +453,22 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff, 
  * contents may change between runs (same n, nnz and voff). Asynchronous. */
 pg_status pg_batch_run(pg_batch *batch, pg_stream_t stream);
 
+/* One run from a HOST copy of the union CSR (page-locked for the copies to
+ * overlap): row_ptr is uploaded into the batch's device CSR, then col in
+ * chunks of whole graphs of one bucket (about chunk_entries entries each, at
+ * least one graph) on copy_stream; after each chunk, stream waits for it and
+ * builds and passes over that chunk's graphs, so the upload of the next
+ * chunks overlaps the work on the earlier ones (a graph's sketches and pass
+ * read only its own rows). Same outputs as pg_batch_run (bit-identical), run
+ * eagerly, not captured. The copies start after the work already enqueued
+ * on stream; when the call returns, stream is ordered after the whole
+ * upload. host_row_ptr: HOST int32 [n+1] from 0 to nnz with the batch's
+ * graph layout (voff); host_col: HOST int32 [nnz]. copy_stream may equal
+ * stream (no overlap). Errors: PG_ERR_INVALID_ARG (NULLs, offsets not from 0
+ * to nnz, chunk_entries < 1), PG_ERR_CUDA. Asynchronous. */
+pg_status pg_batch_run_host(pg_batch *batch, const int32_t *host_row_ptr, const int32_t *host_col,
+                            int64_t chunk_entries, pg_stream_t copy_stream, pg_stream_t stream);
+
 /* Free the host state and the captured graph (not the workspace). NULL is a
  * no-op. */
 pg_status pg_batch_destroy(pg_batch *batch);

@@ -371,6 +371,7 @@ struct pg_batch {
     float *lcc_out;
     double *tri_out;
     std::vector<pg::Bucket> buckets;
+    std::vector<int32_t> voff_h;  // host copy of voff
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaStream_t captured_on;
@@ -482,12 +483,13 @@ pg_status make_buckets(int32_t graphs, const int32_t *voff_host, const pg_batch_
     return PG_OK;
 }
 
-cudaError_t launch_batch_bloom(const pg_batch *bt, const Bucket &bk, cudaStream_t s) {
+// Launches over the vertices [va, vb) of bucket bk (whole graphs).
+cudaError_t launch_batch_bloom(const pg_batch *bt, const Bucket &bk, int32_t va, int32_t vb, cudaStream_t s) {
     BuildParams p{};
     p.row_ptr = bt->g.row_ptr;
     p.col = bt->g.col;
-    p.v_lo = bk.v_lo;
-    p.v_hi = bk.v_hi;
+    p.v_lo = va;
+    p.v_hi = vb;
     p.gid = bt->gid;
     p.voff = bt->voff;
     p.data = bk.data - (int64_t)bk.v_lo * bk.stride;
@@ -505,27 +507,28 @@ cudaError_t launch_batch_bloom(const pg_batch *bt, const Bucket &bk, cudaStream_
     }
 }
 
+cudaError_t launch_build_range(const pg_batch *bt, const Bucket &bk, int32_t va, int32_t vb, cudaStream_t s) {
+    if (bk.bits <= kFlatBuildMaxBits) return launch_batch_bloom(bt, bk, va, vb, s);
+    BatchMap bm{bt->gid, bt->voff, bt->b_of, va};
+    return launch_build_bloom(bt->g.row_ptr + va, bt->g.col, vb - va, bk.bits, bk.b, bt->seed,
+                              bk.data + (int64_t)(va - bk.v_lo) * bk.stride, bk.stride, bt->hub, s, &bm);
+}
+
 pg_status enqueue_builds(pg_batch *bt, cudaStream_t s) {
     for (const Bucket &bk : bt->buckets) {
         if (bk.v_hi <= bk.v_lo) continue;
-        if (bk.bits <= kFlatBuildMaxBits) {
-            PG_TRY_CUDA(launch_batch_bloom(bt, bk, s), "pg_batch: Bloom build");
-        } else {
-            BatchMap bm{bt->gid, bt->voff, bt->b_of, bk.v_lo};
-            PG_TRY_CUDA(launch_build_bloom(bt->g.row_ptr + bk.v_lo, bt->g.col, bk.v_hi - bk.v_lo, bk.bits, bk.b,
-                                           bt->seed, bk.data, bk.stride, bt->hub, s, &bm),
-                        "pg_batch: Bloom build");
-        }
+        PG_TRY_CUDA(launch_build_range(bt, bk, bk.v_lo, bk.v_hi, s), "pg_batch: Bloom build");
     }
     return PG_OK;
 }
 
-cudaError_t launch_pull(const pg_batch *bt, const Bucket &bk, int32_t variant, cudaStream_t s) {
+cudaError_t launch_pull(const pg_batch *bt, const Bucket &bk, int32_t variant, int32_t va, int32_t vb,
+                        cudaStream_t s) {
     PullParams p{};
     p.row_ptr = bt->g.row_ptr;
     p.col = bt->g.col;
-    p.v_lo = bk.v_lo;
-    p.v_hi = bk.v_hi;
+    p.v_lo = va;
+    p.v_hi = vb;
     p.data = bk.data - (int64_t)bk.v_lo * bk.stride;
     p.stride = bk.stride;
     p.l = bk.bits;
@@ -560,7 +563,7 @@ pg_status enqueue_passes(pg_batch *bt, cudaStream_t s) {
     launch_fill_u64(bt->hist, (size_t)bt->hist_bins, 0, s);
     for (const Bucket &bk : bt->buckets) {
         if (bk.v_hi <= bk.v_lo) continue;
-        PG_TRY_CUDA(launch_pull(bt, bk, bk.variant, s), "pg_batch: pass");
+        PG_TRY_CUDA(launch_pull(bt, bk, bk.variant, bk.v_lo, bk.v_hi, s), "pg_batch: pass");
     }
     PG_TRY_CUDA(launch_batch_finalize(bt->hist, bt->hoff, bt->bits_of, bt->b_of, bt->graphs, PG_EST_BF_AND,
                                       bt->tc_out, s),
@@ -642,6 +645,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
         return st;
     }
     carve_batch(g, graphs, cfg_host, bt->buckets, static_cast<uint8_t *>(workspace), bt);
+    bt->voff_h.assign(voff_host, voff_host + graphs + 1);
     // host tables -> device
     std::vector<int64_t> hoff(graphs + 1);
     std::vector<uint32_t> bits(graphs);
@@ -694,7 +698,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
             for (int32_t cand : kPullVariants) {
                 for (int rep = 0; rep < 2; ++rep) {  // first run warms up
                     cudaEventRecord(a, s);
-                    e = launch_pull(bt, bk, cand, s);
+                    e = launch_pull(bt, bk, cand, bk.v_lo, bk.v_hi, s);
                     cudaEventRecord(b, s);
                     if (e == cudaSuccess) e = cudaEventSynchronize(b);
                     if (e != cudaSuccess) break;
@@ -757,6 +761,62 @@ pg_status pg_batch_run(pg_batch *bt, pg_stream_t stream) {
     }
     PG_TRY_CUDA(cudaGraphLaunch(bt->exec, s), "pg_batch_run: launch");
     note_launch();
+    return PG_OK;
+}
+
+pg_status pg_batch_run_host(pg_batch *bt, const int32_t *host_row_ptr, const int32_t *host_col,
+                            int64_t chunk_entries, pg_stream_t copy_stream, pg_stream_t stream) {
+    PG_TRACE("pg_batch_run_host");
+    PG_REQUIRE(bt != nullptr, PG_ERR_INVALID_ARG, "pg_batch_run_host: batch is NULL");
+    const pg_csr &g = bt->g;
+    PG_REQUIRE(host_row_ptr != nullptr && (g.nnz == 0 || host_col != nullptr), PG_ERR_INVALID_ARG,
+               "pg_batch_run_host: host CSR is NULL");
+    PG_REQUIRE(chunk_entries > 0, PG_ERR_INVALID_ARG, "pg_batch_run_host: chunk_entries must be positive");
+    PG_REQUIRE(host_row_ptr[0] == 0 && (int64_t)host_row_ptr[g.n] == g.nnz, PG_ERR_INVALID_ARG,
+               "pg_batch_run_host: host row_ptr must run from 0 to nnz");
+    // the batch's device CSR is this call's upload target (pg_csr holds it as const for the readers)
+    int32_t *dst_rp = const_cast<int32_t *>(g.row_ptr);
+    int32_t *dst_col = const_cast<int32_t *>(g.col);
+    cudaStream_t cs = copy_stream, s = stream;
+    cudaEvent_t ev_start = nullptr, ev_chunk = nullptr;
+    PG_TRY_CUDA(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming), "pg_batch_run_host: event");
+    cudaError_t e = cudaEventCreateWithFlags(&ev_chunk, cudaEventDisableTiming);
+    // the upload overwrites the device CSR: it starts after the work already on the compute stream
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst_rp, host_row_ptr, 4 * ((size_t)g.n + 1), cudaMemcpyDefault, cs);
+    if (e == cudaSuccess) {
+        launch_fill_u64(bt->hist, (size_t)bt->hist_bins, 0, s);
+        e = cudaGetLastError();
+    }
+    const std::vector<int32_t> &vo = bt->voff_h;
+    for (const Bucket &bk : bt->buckets) {
+        // chunks of whole graphs of the bucket, about chunk_entries CSR entries each (at least one graph)
+        for (int32_t g0 = bk.g_lo; e == cudaSuccess && g0 < bk.g_hi;) {
+            const int64_t x0 = host_row_ptr[vo[g0]];
+            int32_t g1 = g0 + 1;
+            while (g1 < bk.g_hi && (int64_t)host_row_ptr[vo[g1 + 1]] - x0 <= chunk_entries) ++g1;
+            const int32_t va = vo[g0], vb = vo[g1];
+            const int64_t x1 = host_row_ptr[vb];
+            if (x1 > x0)
+                e = cudaMemcpyAsync(dst_col + x0, host_col + x0, 4 * (size_t)(x1 - x0), cudaMemcpyDefault, cs);
+            if (e == cudaSuccess) e = cudaEventRecord(ev_chunk, cs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_chunk, 0);
+            if (e == cudaSuccess && vb > va) e = launch_build_range(bt, bk, va, vb, s);
+            if (e == cudaSuccess && vb > va) e = launch_pull(bt, bk, bk.variant, va, vb, s);
+            g0 = g1;
+        }
+    }
+    // the buckets cover every graph (voff runs from 0 to n), so the chunks copied all of col;
+    // order the stream after the whole upload
+    if (e == cudaSuccess) e = cudaEventRecord(ev_chunk, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_chunk, 0);
+    if (e == cudaSuccess)
+        e = launch_batch_finalize(bt->hist, bt->hoff, bt->bits_of, bt->b_of, bt->graphs, PG_EST_BF_AND, bt->tc_out,
+                                  s);
+    cudaEventDestroy(ev_start);
+    if (ev_chunk) cudaEventDestroy(ev_chunk);
+    PG_TRY_CUDA(e, "pg_batch_run_host");
     return PG_OK;
 }
 

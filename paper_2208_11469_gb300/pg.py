@@ -36,7 +36,8 @@ SYMBOLS = [
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
     "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick", "pg_clique4_workspace_bytes", "pg_clique4_count",
-    "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_destroy",
+    "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_run_host",
+    "pg_batch_destroy",
     "pg_server_reserved_bytes", "pg_server_create", "pg_submit", "pg_submit_many", "pg_poll_many", "pg_poll",
     "pg_cancel", "pg_server_stats_get", "pg_server_destroy",
 ]
@@ -174,6 +175,7 @@ def lib() -> ctypes.CDLL:
                 "pg_batch_create": (i32, [P(Csr), i32, vp, P(BatchConfig), u32, vp, sz, vp, vp, vp, vp,
                                           P(vp)]),
                 "pg_batch_run": (i32, [vp, vp]),
+                "pg_batch_run_host": (i32, [vp, vp, vp, i64, vp, vp]),
                 "pg_batch_destroy": (i32, [vp]),
                 "pg_server_reserved_bytes": (sz, [P(Csr), P(ServerOpts)]),
                 "pg_server_create": (i32, [P(Csr), P(P(SketchDesc)), i32, vp, sz, P(ServerOpts), P(vp)]),
@@ -634,6 +636,25 @@ class Batch:
 
     def run(self, stream: int | None = None):
         _check(lib().pg_batch_run(self._h, _stream() if stream is None else stream), "pg_batch_run")
+
+    def run_host(self, host_row_ptr: torch.Tensor, host_col: torch.Tensor, chunk_entries: int | None = None,
+                 copy_stream=None):
+        """pg_batch_run_host: one run from host tensors of the union CSR
+        (page-locked for overlap), uploaded in chunks of whole graphs on
+        copy_stream (a torch.cuda.Stream; None: a stream of this module)
+        while the current stream works on the chunks already copied."""
+        assert host_row_ptr.device.type == "cpu" and host_col.device.type == "cpu"
+        assert host_row_ptr.dtype == torch.int32 and host_col.dtype == torch.int32
+        assert host_row_ptr.is_contiguous() and host_col.is_contiguous()
+        if chunk_entries is None:
+            chunk_entries = max(1 << 20, self.g.nnz // 16)
+        if copy_stream is None:
+            global _upload_stream
+            if _upload_stream is None:
+                _upload_stream = torch.cuda.Stream(device=self.g.device)
+            copy_stream = _upload_stream
+        _check(lib().pg_batch_run_host(self._h, host_row_ptr.data_ptr(), host_col.data_ptr(), int(chunk_entries),
+                                       copy_stream.cuda_stream, _stream()), "pg_batch_run_host")
 
     def results(self):
         """Per-graph dicts of the triangle-count result (synchronises)."""

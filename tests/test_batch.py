@@ -183,6 +183,46 @@ def test_batch_matches_single_graph_calls(pg):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("chunk,own_stream", [(1, True), (5000, True), (1 << 30, True), (5000, False)])
+def test_run_host_matches_device_run(pg, chunk, own_stream):
+    """pg_batch_run_host uploads the union CSR in chunks of whole graphs while
+    it works on the chunks already copied: after it, the device CSR equals the
+    host one and every output is bit-identical to a run on that CSR. The host
+    CSR differs from the one the batch was created on (inside each graph the
+    column ids are mapped by a permutation of its vertices), so a run that
+    did not upload would be caught."""
+    parts, cfg = _assign(_mix())
+    rp, cl, voff = synth.block_diagonal(parts)
+    gen = torch.Generator().manual_seed(7)
+    perm = torch.arange(rp.numel() - 1, dtype=torch.int64)
+    for i in range(len(voff) - 1):
+        a, b = int(voff[i]), int(voff[i + 1])
+        if b > a:
+            perm[a:b] = a + torch.randperm(b - a, generator=gen)
+    cl2 = perm[cl.long()].to(torch.int32)
+    dev_rp, dev_cl = rp.cuda(), cl.cuda()
+    batch = pg.Batch(pg.graph(dev_rp, dev_cl, build_index=False), voff, cfg, seed=5, want_tri=True)
+    dev_cl.copy_(cl2.cuda())
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        batch.run()
+    side.synchronize()
+    want = (batch.results(), batch.lcc.cpu().numpy().copy(), batch.tri.cpu().numpy().copy())
+    dev_cl.copy_(cl.cuda())
+    batch.lcc.fill_(-1.0)
+    batch.tri.fill_(-1.0)
+    torch.cuda.synchronize()
+    cs = torch.cuda.Stream() if own_stream else torch.cuda.current_stream()
+    batch.run_host(rp.pin_memory(), cl2.pin_memory(), chunk_entries=chunk, copy_stream=cs)
+    torch.cuda.synchronize()
+    assert torch.equal(dev_cl.cpu(), cl2) and torch.equal(dev_rp.cpu(), rp)
+    assert batch.results() == want[0]
+    np.testing.assert_array_equal(batch.lcc.cpu().numpy(), want[1])
+    np.testing.assert_array_equal(batch.tri.cpu().numpy(), want[2])
+    batch.close()
+
+
+@pytest.mark.gpu
 def test_64_bit_build_with_hub_rows(pg):
     """The 64-bit buckets use their own builder (one warp walks 32 rows'
     entries, so a hub row is walked by one warp): a graph with a 9500-entry
