@@ -38,9 +38,11 @@ namespace {
 // does not depend on the order of the adds or on the work mapping.
 //
 // Work order: 32-vertex groups (row r of a group is held by lane r), `chunk`
-// consecutive groups per warp chunk, chunks dealt to the warps round-robin so
-// that at any time the warps work inside a window of a few graphs whose
-// sketch rows stay in L2. A warp walks its group's entries (the rows are
+// consecutive groups per work chunk, chunks taken by the warps in order from
+// a global counter, so that at any time the warps work inside a window of a
+// few graphs whose sketch rows stay in L2 (a static round-robin deal let
+// warps that met hub rows fall behind until the window outgrew L2). The last
+// block to finish resets the counter for the next launch. A warp walks its group's entries (the rows are
 // contiguous in the CSR) 32 at a time, one entry per lane with coalesced
 // loads whatever the degrees: a 5-step search over the row ends held by the
 // lanes gives each entry's row, and one inclusive warp scan of the 32
@@ -63,7 +65,8 @@ struct PullParams {
     unsigned long long *hist;        // per-graph histograms (zeroed before the pass)
     float *lcc;
     double *tri;                     // or null
-    int32_t chunk;                   // groups per warp chunk
+    int32_t chunk;                   // groups per work chunk
+    int32_t *queue;                  // [2]: next chunk, blocks done; zero between launches
 };
 
 // The W payload words of a sketch row (W = l / 32: 2 for 64-bit filters, whose
@@ -137,15 +140,17 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_pull(PullParams p) {
     __syncthreads();
 
     const unsigned lane = lane_id();
-    const int64_t warp = ((int64_t)blockIdx.x * kPullThreads + threadIdx.x) >> 5;
-    const int64_t warps = (int64_t)gridDim.x * kPullWarps;
     const int64_t groups = ((int64_t)p.v_hi - p.v_lo + 31) / 32;
     const int64_t chunks = (groups + p.chunk - 1) / p.chunk;
     int32_t warp_g = -1;  // graph of the warp's shared histogram
 
-    for (int64_t ch = warp; ch < chunks; ch += warps) {
+    for (;;) {
+        int32_t ch = 0;
+        if (lane == 0) ch = atomicAdd(p.queue, 1);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= chunks) break;
         for (int gi = 0; gi < p.chunk; ++gi) {
-            const int64_t grp = ch * p.chunk + gi;
+            const int64_t grp = (int64_t)ch * p.chunk + gi;
             if (grp >= groups) break;
             const int32_t v0 = p.v_lo + (int32_t)(grp * 32);
             const int32_t u = v0 + (int32_t)lane;
@@ -211,6 +216,15 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_pull(PullParams p) {
         }
     }
     flush_hist(p, hw, warp_g, lane);
+    // every warp of every block has left the loop once the last block gets here: reset the queue
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(p.queue + 1, 1) == (int)gridDim.x - 1) {
+            p.queue[0] = 0;
+            p.queue[1] = 0;
+        }
+    }
 }
 
 template <int W>
@@ -367,6 +381,7 @@ struct pg_batch {
     uint64_t *hist;
     int64_t hist_bins;
     int32_t *hub;
+    int32_t *queue;  // work counter of the pull pass
     pg_tc_result *tc_out;
     float *lcc_out;
     double *tri_out;
@@ -428,6 +443,7 @@ size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, 
     uint8_t *b = take((size_t)graphs + 4);
     uint8_t *hist = take(8 * (size_t)bins + 8);
     uint8_t *hub = take(build_workspace_bytes(g->nnz));
+    uint8_t *queue = take(16);
     for (Bucket &bk : buckets) {
         uint8_t *table = take(intersect_table_bytes(PG_SK_BLOOM, bk.bits, 0));
         uint8_t *data = take((size_t)(bk.v_hi - bk.v_lo) * (size_t)bk.stride + 16);
@@ -445,6 +461,7 @@ size_t carve_batch(const pg_csr *g, int32_t graphs, const pg_batch_config *cfg, 
         out->hist = reinterpret_cast<uint64_t *>(hist);
         out->hist_bins = bins;
         out->hub = reinterpret_cast<int32_t *>(hub);
+        out->queue = reinterpret_cast<int32_t *>(queue);
     }
     return off;
 }
@@ -539,6 +556,7 @@ cudaError_t launch_pull(const pg_batch *bt, const Bucket &bk, int32_t variant, i
     p.lcc = bt->lcc_out;
     p.tri = bt->tri_out;
     p.chunk = variant;
+    p.queue = bt->queue;
     switch (bk.bits) {
         case 64: return run_pull<2>(p, s);
         case 128: return run_pull<4>(p, s);
@@ -661,6 +679,7 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff_h
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt->hoff, hoff.data(), 8 * hoff.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt->bits_of, bits.data(), 4 * bits.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bt->b_of, bs.data(), bs.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bt->queue, 0, 16, s);
     if (e == cudaSuccess) {
         k_graph_ids<<<std::min(graphs, 4096), 256, 0, s>>>(bt->voff, graphs, bt->gid);
         note_launch();
