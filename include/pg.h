@@ -447,10 +447,13 @@ pg_status pg_batch_create(const pg_csr *g, int32_t graphs, const int32_t *voff, 
                           float *lcc, double *tri, pg_stream_t stream, pg_batch **out);
 
 /* One run: sketches and pass of every graph (the pass writes LCC and
- * triangles per vertex), then the per-graph triangle counts. On a non-default stream the first run captures
- * the sequence as a CUDA graph (for that stream) and every run launches it;
- * on the default stream (NULL) the kernels are launched one by one. The CSR
- * contents may change between runs (same n, nnz and voff). Asynchronous. */
+ * triangles per vertex), then the per-graph triangle counts. On a
+ * non-default stream the first run captures the sequence as a CUDA graph
+ * (for that stream) and every run launches it; on the default stream (NULL)
+ * the kernels are launched one by one. The CSR contents may change between
+ * runs (same n, nnz and voff). Runs of one batch use its workspace (sketches,
+ * histograms, the pass's work counter) and must not overlap in time: order
+ * runs on different streams with events. Asynchronous. */
 pg_status pg_batch_run(pg_batch *batch, pg_stream_t stream);
 
 /* One run from a HOST copy of the union CSR (page-locked for the copies to
