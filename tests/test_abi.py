@@ -131,3 +131,36 @@ def test_sketch_file_header_errors(tmp_path):
     good.write_bytes(struct.pack("<8siiIIIIiiqq8s", b"PGSKTCH1", 1, 1, 448, 2, 0, 7, 3, 0, 64, 192, bytes(8)))
     assert L.pg_sketch_load_header(str(good).encode(), ctypes.byref(d)) == 0
     assert (d.kind, d.bits, d.b, d.k, d.seed, d.n, d.stride_bytes) == (1, 448, 2, 0, 7, 3, 64)
+
+
+def test_upload_and_host_run_argument_errors(L):
+    """pg_upload_build and pg_batch_run_host check their host-side arguments
+    before any CUDA call: a NULL batch or host CSR, host offsets that do not
+    run from 0 to nnz, a non-positive chunk size, a bad sketch and a small
+    build workspace are refused with their codes."""
+    import numpy as np
+    from paper_2208_11469_gb300 import pg
+    byref = ctypes.byref
+    g = _csr(n=4, nnz=6)
+    rp = np.array([0, 2, 3, 5, 6], dtype=np.int32)
+    cl = np.array([1, 2, 0, 0, 3, 2], dtype=np.int32)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    sk = (pg.SketchDesc * 1)(pg.SketchDesc(pg.SK_BLOOM, 256, 2, 0, 1, 4, 32, 0x3000))
+    ws_need = L.pg_build_workspace_bytes(byref(g))
+
+    def up(rp_, cl_, sks, count, ws_bytes=ws_need, chunk=2):
+        return L.pg_upload_build(rp_, cl_, byref(g), sks, count, ctypes.c_void_p(0x4000), ws_bytes, chunk, None,
+                                 None)
+
+    assert up(None, vp(cl), sk, 1) == -1
+    assert up(vp(rp), None, sk, 1) == -1
+    bad = rp.copy()
+    bad[-1] = 7  # does not end at nnz
+    assert up(vp(bad), vp(cl), sk, 1) == -1
+    assert "0 to nnz" in L.pg_last_error().decode()
+    assert up(vp(rp), vp(cl), sk, 1, chunk=0) == -1
+    assert up(vp(rp), vp(cl), sk, 1, ws_bytes=ws_need - 1 if ws_need > 0 else 0) in (-1, -4)
+    wrong = (pg.SketchDesc * 1)(pg.SketchDesc(pg.SK_BLOOM, 256, 2, 0, 1, 5, 32, 0x3000))  # rows != n
+    assert up(vp(rp), vp(cl), wrong, 1) == -1
+    assert up(vp(rp), vp(cl), None, 1) == -1
+    assert L.pg_batch_run_host(None, vp(rp), vp(cl), 16, None, None) == -1
