@@ -8,7 +8,8 @@ and the CUDA library never imports it.
 Every function restates one passage of Besta et al., SC'22 (ProbGraph):
   * sketches:   Sec. II-C (Bloom filter, k-Hash, 1-Hash)
   * estimators: Eq. (est_ss_bf), Eq. (bf_int), Eq. (limit_xs),
-                Eq. (est_int_mh) and Sec. IV-D
+                Eq. (est_int_mh), Sec. IV-D and the KMV estimator of
+                Sec. IX (est_kmv: oracle only, not built on the GPU yet)
   * reductions: the TC estimator of Sec. VII, (1/3) * sum over edges;
                 per-vertex triangles and the local clustering coefficient
                 (Sec. III-A "clustering coefficient", standard local form);
@@ -310,6 +311,29 @@ def est_minhash(c, K, size_x, size_y):
     with np.errstate(divide="ignore", invalid="ignore"):
         J = np.where(K > 0, c / np.where(K > 0, K, 1.0), 0.0)
     return J / (1.0 + J) * s
+
+
+def kmv_union(hx, hy, k: int) -> np.ndarray:
+    """Sec. IX: the KMV sketch of X ∪ Y, the k smallest distinct values of
+    the two sketches' hash values (hx, hy: ascending uint32 hashes)."""
+    merged = np.union1d(np.asarray(hx, dtype=np.uint64), np.asarray(hy, dtype=np.uint64))
+    return merged[:k]
+
+
+def est_kmv(hx, hy, size_x: int, size_y: int, k: int) -> float:
+    """Sec. IX: |X ∩ Y|^ = |X| + |Y| - |X ∪ Y|^, with |X ∪ Y|^ = (k - 1) /
+    max K_{X∪Y} and the 32-bit hashes mapped into (0, 1] by h -> (h + 1) /
+    2^32. hx, hy: the sketches' hash values (the k smallest hashes of each
+    set, all of them for a set of at most k elements: a 1-Hash row). Reading
+    T: a union sketch of fewer than k values holds the whole union, whose
+    size is then its length (the estimator needs k values). Not built in the
+    CUDA library: parity unpinned there; pinned here against exact sizes."""
+    u = kmv_union(hx, hy, k)
+    if u.size < k:
+        union = float(u.size)
+    else:
+        union = (k - 1) / ((float(u[-1]) + 1.0) / 4294967296.0)
+    return float(size_x) + float(size_y) - union
 
 
 # --------------------------------------------------------------------------
