@@ -216,6 +216,12 @@ pg_status pg_sketch_load(pg_sketch *sk, const char *path, pg_stream_t stream);
                                 (read as l - 1 when U = l); per-edge aux = U; pass kernels of any width */
 #define PG_EST_BF_SS       7 /* the single-set Bloom estimator on the AND filter (Sec. VIII):
                                 log(1 - B1/l) / (b log(1 - 1/l)), B1 = l read as l - 1 */
+#define PG_EST_1H_KMV      8 /* Sec. IX, KMV on the 1-Hash rows: d_u + d_v - (k - 1) / h_k, h_k the
+                                k-th smallest hash of the two rows' union mapped into (0, 1] as
+                                (h + 1) / 2^32; a union of fewer than k values is counted exactly.
+                                Per-edge and per-pair outputs only (pg_jaccard_pairs,
+                                pg_similarity_pairs, pg_edge_counts without hist): calls that
+                                reduce estimates into totals return PG_ERR_UNSUPPORTED */
 
 /* Graph-level result, written to a DEVICE pg_tc_result. */
 typedef struct pg_tc_result {

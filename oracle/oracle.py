@@ -34,7 +34,7 @@ _lock = threading.Lock()
 _lib = None
 
 EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
-EST_BF_OR, EST_BF_SS = 6, 7
+EST_BF_OR, EST_BF_SS, EST_1H_KMV = 6, 7, 8
 
 
 def build(force: bool = False) -> str:
@@ -370,6 +370,14 @@ def pair_counts(row_ptr, col, est: int, sk, pu, pv, *, seed=1):
     if est in (EST_1H, EST_1H_LITERAL):
         cl, cu, K = onehash_pairs(sk, seed, row_ptr, pu, pv)
         return {"count": cu, "K": K, "c_lit": cl}
+    if est == EST_1H_KMV:
+        cl, cu, K = onehash_pairs(sk, seed, row_ptr, pu, pv)
+        H = onehash_values(sk, seed)
+        d = degrees(row_ptr)
+        k = sk.shape[1]
+        kmv = np.array([est_kmv(H[u][H[u] != 0xFFFFFFFF], H[v][H[v] != 0xFFFFFFFF], d[u], d[v], k)
+                        for u, v in zip(np.asarray(pu), np.asarray(pv))], dtype=np.float64)
+        return {"count": cu, "K": K, "c_lit": cl, "kmv": kmv}
     raise ValueError(est)
 
 
@@ -394,6 +402,8 @@ def pair_estimates(row_ptr, est: int, counts: dict, pu, pv, *, l=256, b=2, k=16)
     if est == EST_1H_LITERAL:
         # the formula as printed: J = |M1_X ∩ M1_Y| / k
         return est_minhash(counts["c_lit"], np.full(len(c), k), d[pu], d[pv])
+    if est == EST_1H_KMV:
+        return counts["kmv"]
     raise ValueError(est)
 
 

@@ -37,6 +37,8 @@ struct TraceRange {
 pg_status check_graph(const pg_csr *g);
 pg_status check_sketch(const pg_csr *g, const pg_sketch *sk);
 pg_status check_estimator(const pg_sketch *sk, int32_t est);
+// PG_ERR_UNSUPPORTED for estimators without totals (KMV) in calls that reduce them.
+pg_status check_totals(int32_t est, const char *fn);
 
 struct DeviceInfo {
     int sm_count;

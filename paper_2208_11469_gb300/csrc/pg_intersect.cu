@@ -637,8 +637,8 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
             }
         }
         __syncwarp();
-        // phase 1: the K smallest distinct values of the union
-        uint32_t i = 0, j = 0, K = 0, cun = 0;
+        // phase 1: the K smallest distinct values of the union (hK: the last of them)
+        uint32_t i = 0, j = 0, K = 0, cun = 0, hK = 0;
         for (uint32_t st = 0; st < k; ++st) {
             const bool ha = i < la, hb = j < lb;
             if (!__any_sync(0xffffffffu, ha || hb)) break;
@@ -647,6 +647,7 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
             const bool tb = hb && (!ha || y <= x);
             K += (ha || hb);
             cun += (ta && tb);
+            if (ha || hb) hK = ta ? x : y;
             i += ta;
             j += tb;
         }
@@ -676,7 +677,13 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
             const int ti = (p.est == PG_EST_1H_LITERAL) ? (int)k * hk + (int)clit : (int)K * hk + (int)cun;
             V = minhash_fixed(tabV[ti], ds, fx_ok);
             if (!fx_ok) big = tab[ti] * (double)ds;
-            const float est_f = tabF[ti] * (float)ds;
+            float est_f = tabF[ti] * (float)ds;
+            if (p.est == PG_EST_1H_KMV) {
+                // Sec. IX: |X ∪ Y| ~ (k - 1) / max of the union's k smallest hashes in (0, 1];
+                // a union of fewer than k values is the whole union (per-edge outputs only)
+                const double uni = K < k ? (double)K : (double)(k - 1) * 4294967296.0 / ((double)hK + 1.0);
+                est_f = (float)((double)ds - uni);
+            }
             if (p.aux) p.aux[e] = (int32_t)(K | (clit << 16));
             if (p.count) p.count[e] = (int32_t)((p.est == PG_EST_1H_LITERAL) ? clit : cun);
             write_sims(p, e, est_f, cdu, cdv);

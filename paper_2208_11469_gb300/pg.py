@@ -24,7 +24,7 @@ ERR = {0: "PG_OK", -1: "PG_ERR_INVALID_ARG", -2: "PG_ERR_INVALID_GRAPH", -3: "PG
        -8: "PG_ERR_BUSY", -9: "PG_ERR_UNSUPPORTED", -10: "PG_ERR_CANCELLED"}
 SK_BLOOM, SK_KHASH, SK_1HASH = 1, 2, 3
 EST_EXACT, EST_BF_AND, EST_BF_L, EST_KH, EST_1H, EST_1H_LITERAL = 0, 1, 2, 3, 4, 5
-EST_BF_OR, EST_BF_SS = 6, 7
+EST_BF_OR, EST_BF_SS, EST_1H_KMV = 6, 7, 8
 CSR_CODES = {0: "ok", 1: "bad_row_ptr", 2: "out_of_range", 3: "unsorted", 4: "self_loop", 5: "asymmetric"}
 
 # Every symbol include/pg.h declares.

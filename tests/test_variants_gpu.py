@@ -96,6 +96,8 @@ def test_bloom_variants_every_output(pg, name, est, l, b):
     (O.EST_BF_OR, "bloom", dict(l=256, b=2)),
     (O.EST_KH, "khash", dict(k=32)),
     (O.EST_1H, "onehash", dict(k=32)),
+    (O.EST_1H_KMV, "onehash", dict(k=32)),
+    (O.EST_1H_KMV, "onehash", dict(k=8)),
 ])
 def test_similarity_pairs(pg, est, kind, kw):
     rp, cl = _graph("rmat12")
@@ -116,7 +118,8 @@ def test_similarity_pairs(pg, est, kind, kw):
     counts = O.pair_counts(rp, cl, est, osk, pu, pv, seed=2)
     e = O.pair_estimates(rp, est, counts, pu, pv, l=kw.get("l", 256), b=kw.get("b", 2), k=kw.get("k", 16))
     want = O.similarities(rp, e, pu, pv)
-    atol = 1e-3 if est == O.EST_BF_OR else 1e-6
+    # OR and KMV estimates cancel (|X| + |Y| minus a similar number): an absolute floor
+    atol = 1e-3 if est in (O.EST_BF_OR, O.EST_1H_KMV) else 1e-6
     for nm in ("cn", "jac", "overlap", "total"):
         g_ = got[nm].cpu().numpy()
         _close(g_[ok], want[nm], RTOL_F32, atol if nm in ("cn", "total") else 1e-5)
@@ -134,3 +137,27 @@ def test_variant_pairs_match_edges(pg):
     c1, a1, _ = pg.edge_counts(g, sk, pg.EST_BF_OR, pairs, want_aux=True)
     c2, a2, _ = pg.edge_counts(g, sk, pg.EST_BF_OR, None, want_aux=True)
     assert torch.equal(c1, c2) and torch.equal(a1, a2)
+
+
+@pytest.mark.parametrize("name", ["er4096", "rmat12", "hubs"])
+def test_kmv_upper_edges(pg, name):
+    """KMV (Sec. IX) on the 1-Hash rows over every upper edge (pairs = NULL),
+    against the oracle; the calls that reduce estimates into totals refuse it."""
+    rp, cl = _graph(name)
+    g = pg.graph(torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda())
+    k = 16
+    sk = pg.build_minhash(g, pg.SK_1HASH, k, seed=3)
+    cn, jac = pg.jaccard_pairs(g, sk, pg.EST_1H_KMV)
+    eu, ev = O.upper_edges(rp, cl)
+    osk = O.sketch(rp, cl, "onehash", k=k, seed=3)
+    counts = O.pair_counts(rp, cl, O.EST_1H_KMV, osk, eu, ev, seed=3)
+    e = O.pair_estimates(rp, O.EST_1H_KMV, counts, eu, ev, k=k)
+    want = O.similarities(rp, e, eu, ev)
+    _close(cn.cpu().numpy(), want["cn"], RTOL_F32, 1e-3)
+    _close(jac.cpu().numpy(), want["jac"], RTOL_F32, 1e-5)
+    c, a, _ = pg.edge_counts(g, sk, pg.EST_1H_KMV, None, want_aux=True)
+    np.testing.assert_array_equal(c.cpu().numpy(), counts["count"])
+    for call in (lambda: pg.triangle_count(g, sk, pg.EST_1H_KMV), lambda: pg.clustering(g, sk, pg.EST_1H_KMV)):
+        with pytest.raises(pg.PGError) as ei:
+            call()
+        assert ei.value.status == -9
