@@ -9,7 +9,7 @@ Every function restates one passage of Besta et al., SC'22 (ProbGraph):
   * sketches:   Sec. II-C (Bloom filter, k-Hash, 1-Hash)
   * estimators: Eq. (est_ss_bf), Eq. (bf_int), Eq. (limit_xs),
                 Eq. (est_int_mh), Sec. IV-D and the KMV estimator of
-                Sec. IX (est_kmv: oracle only, not built on the GPU yet)
+                Sec. IX (est_kmv)
   * reductions: the TC estimator of Sec. VII, (1/3) * sum over edges;
                 per-vertex triangles and the local clustering coefficient
                 (Sec. III-A "clustering coefficient", standard local form);
@@ -326,8 +326,7 @@ def est_kmv(hx, hy, size_x: int, size_y: int, k: int) -> float:
     2^32. hx, hy: the sketches' hash values (the k smallest hashes of each
     set, all of them for a set of at most k elements: a 1-Hash row). Reading
     T: a union sketch of fewer than k values holds the whole union, whose
-    size is then its length (the estimator needs k values). Not built in the
-    CUDA library: parity unpinned there; pinned here against exact sizes."""
+    size is then its length (the estimator needs k values)."""
     u = kmv_union(hx, hy, k)
     if u.size < k:
         union = float(u.size)
