@@ -219,9 +219,9 @@ pg_status pg_sketch_load(pg_sketch *sk, const char *path, pg_stream_t stream);
 #define PG_EST_1H_KMV      8 /* Sec. IX, KMV on the 1-Hash rows: d_u + d_v - (k - 1) / h_k, h_k the
                                 k-th smallest hash of the two rows' union mapped into (0, 1] as
                                 (h + 1) / 2^32; a union of fewer than k values is counted exactly.
-                                Per-edge and per-pair outputs only (pg_jaccard_pairs,
-                                pg_similarity_pairs, pg_edge_counts without hist): calls that
-                                reduce estimates into totals return PG_ERR_UNSUPPORTED */
+                                Totals: the 1-Hash histograms plus the exact 128-bit sum (x 2^-52)
+                                of the real union estimates (two extra bins); est_tc_alt = the
+                                c_union / K estimate of the same edges */
 
 /* Graph-level result, written to a DEVICE pg_tc_result. */
 typedef struct pg_tc_result {
@@ -237,10 +237,12 @@ typedef struct pg_tc_result {
 } pg_tc_result;
 
 /* Number of uint64 histogram bins pg_edge_counts fills for a sketch/estimator:
- * Bloom: l+1 (count of edges per popcount); k-Hash: 2(k+1) (edges per match
- * count, then sum of d_u + d_v per match count); 1-Hash: 2(k+1)^2 + 2(k+1)
- * ((c_union, K) edge counts, their degree sums, then c_lit edge counts and
- * degree sums); exact: 0. */
+ * Bloom: l+1 (count of edges per popcount; OR: per union popcount, plus one
+ * bin with the sum of d_u + d_v); k-Hash: 2(k+1) (edges per match count, then
+ * sum of d_u + d_v per match count); 1-Hash: 2(k+1)^2 + 2(k+1) ((c_union, K)
+ * edge counts, their degree sums, then c_lit edge counts and degree sums),
+ * plus two for KMV (the 128-bit sum x 2^52 of the real union estimates, low
+ * word first); exact: 0. */
 int64_t pg_hist_bins(const pg_sketch *sk, int32_t estimator);
 
 /* Workspace bytes for pg_triangle_count / pg_clustering / pg_jaccard_pairs /

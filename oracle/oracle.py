@@ -448,7 +448,8 @@ def analyze(row_ptr, col, est: int, *, l=256, b=2, k=16, seed=1, sk=None):
     rp, cl = _csr(row_ptr, col)
     n = rp.size - 1
     kind = {EST_BF_AND: "bloom", EST_BF_L: "bloom", EST_BF_OR: "bloom", EST_BF_SS: "bloom", EST_KH: "khash",
-            EST_1H: "onehash", EST_1H_LITERAL: "onehash"}.get(est)
+            EST_1H: "onehash", EST_1H_LITERAL: "onehash",
+            EST_1H_KMV: "onehash"}.get(est)
     if sk is None and kind is not None:
         sk = sketch(rp, cl, kind, l=l, b=b, k=k, seed=seed)
     eu, ev = upper_edges(rp, cl)

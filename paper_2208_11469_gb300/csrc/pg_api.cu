@@ -117,14 +117,6 @@ pg_status check_estimator(const pg_sketch *sk, int32_t est) {
     }
 }
 
-// The KMV estimate is a real number per edge (no integer histogram carries it),
-// so the calls that reduce estimates into totals do not take it.
-pg_status check_totals(int32_t est, const char *fn) {
-    PG_REQUIRE(est != PG_EST_1H_KMV, PG_ERR_UNSUPPORTED,
-               "%s: the KMV estimator gives per-edge and per-pair outputs only", fn);
-    return PG_OK;
-}
-
 namespace {
 
 // Workspace layout of the analysis calls:
@@ -402,8 +394,6 @@ pg_status pg_triangle_count(const pg_csr *g, const void *index, const pg_sketch 
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
     if (st) return st;
-    st = check_totals(estimator, "pg_triangle_count");
-    if (st) return st;
     PG_REQUIRE(out != nullptr && (reinterpret_cast<uintptr_t>(out) & 7u) == 0, PG_ERR_INVALID_ARG,
                "out must be an 8-byte aligned device pg_tc_result");
     const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
@@ -431,8 +421,6 @@ pg_status pg_clustering(const pg_csr *g, const void *index, const pg_sketch *sk,
     PG_TRACE("pg_clustering");
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
-    if (st) return st;
-    st = check_totals(estimator, "pg_clustering");
     if (st) return st;
     PG_REQUIRE(g->n == 0 || lcc != nullptr || tri != nullptr, PG_ERR_INVALID_ARG,
                "lcc and tri are both NULL");
@@ -546,8 +534,6 @@ pg_status pg_edge_counts(const pg_csr *g, const void *index, const pg_sketch *sk
     }
     eo.aux = aux;
     if (hist) {
-        st = check_totals(estimator, "pg_edge_counts (hist)");
-        if (st) return st;
         PG_REQUIRE((reinterpret_cast<uintptr_t>(hist) & 7u) == 0, PG_ERR_INVALID_ARG,
                    "hist must be 8-byte aligned");
         eo.hist = hist;
@@ -564,8 +550,6 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
     PG_TRACE("pg_analyze");
     Workspace w;
     pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
-    if (st) return st;
-    st = check_totals(estimator, "pg_analyze");
     if (st) return st;
     PG_REQUIRE(out != nullptr, PG_ERR_INVALID_ARG, "outputs is NULL");
     PG_REQUIRE((reinterpret_cast<uintptr_t>(out->tri) & 7u) == 0 &&

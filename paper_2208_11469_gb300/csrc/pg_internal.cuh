@@ -37,8 +37,6 @@ struct TraceRange {
 pg_status check_graph(const pg_csr *g);
 pg_status check_sketch(const pg_csr *g, const pg_sketch *sk);
 pg_status check_estimator(const pg_sketch *sk, int32_t est);
-// PG_ERR_UNSUPPORTED for estimators without totals (KMV) in calls that reduce them.
-pg_status check_totals(int32_t est, const char *fn);
 
 struct DeviceInfo {
     int sm_count;
@@ -161,7 +159,7 @@ struct EdgeOutputs {
     uint64_t *hist;     // [bins] (zeroed by caller) or null
 };
 // Histogram bins of a pass: Bloom l + 1 (plus one for the OR estimator's
-// degree sum), k-Hash 2 (k + 1), 1-Hash 2 (k + 1)^2 + 2 (k + 1).
+// degree sum), k-Hash 2 (k + 1), 1-Hash 2 (k + 1)^2 + 2 (k + 1) (plus two for the KMV sum).
 int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k, int32_t estimator);
 size_t intersect_table_bytes(int32_t kind, uint32_t l, uint32_t k);
 // Enqueue the estimator-table kernel (into table_ws) and the intersection

@@ -579,6 +579,31 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
 // aggregated over the lanes with the same bin (one shared atomic per bin).
 constexpr int kOneHashWarps = kThreads / 32;
 
+// x (a double in [0, 2^75)) added to the 128-bit integer (lo, hi) as x * 2^52:
+// exact for x >= 1 (whose last significant bit is at 2^-52 or above); a
+// positive x below 1 would lose its bits below 2^-52 (the KMV union
+// estimates are 0 or at least k - 1 >= 1).
+__device__ __forceinline__ void add_fixed52(unsigned long long &lo, unsigned long long &hi, double x) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex == 0) return;  // zero (or subnormal)
+    const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - 1023;  // x = mant * 2^(sh - 52), so x * 2^52 = mant * 2^sh
+    unsigned long long xl, xh;
+    if (sh >= 64) {
+        xl = 0ull;
+        xh = mant << (sh - 64);
+    } else if (sh >= 0) {
+        xl = mant << sh;
+        xh = sh == 0 ? 0ull : (mant >> (64 - sh));
+    } else {
+        xl = -sh < 64 ? (mant >> -sh) : 0ull;
+        xh = 0ull;
+    }
+    lo += xl;
+    hi += xh + (lo < xl);
+}
+
 template <bool PAIRS>
 __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -614,6 +639,10 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
     int64_t w0, w1;
     warp_range<PAIRS>(p, w0, w1);
     const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
+    const bool kmv = p.est == PG_EST_1H_KMV;
+    // KMV totals: this lane's sum of the real union estimates (k - 1) 2^32 / (h_k + 1) of its
+    // edges whose union sketch is full, as an exact 128-bit integer x 2^-52
+    unsigned long long rlo = 0ull, rhi = 0ull;
     for (int32_t it = 0; it < iters; ++it) {
         const int64_t e = w0 + (int64_t)it * 32 + lane;
         int32_t cu, cv, cdu, cdv;
@@ -678,11 +707,15 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
             V = minhash_fixed(tabV[ti], ds, fx_ok);
             if (!fx_ok) big = tab[ti] * (double)ds;
             float est_f = tabF[ti] * (float)ds;
-            if (p.est == PG_EST_1H_KMV) {
+            if (kmv) {
                 // Sec. IX: |X ∪ Y| ~ (k - 1) / max of the union's k smallest hashes in (0, 1];
-                // a union of fewer than k values is the whole union (per-edge outputs only)
+                // a union of fewer than k values is the whole union
                 const double uni = K < k ? (double)K : (double)(k - 1) * 4294967296.0 / ((double)hK + 1.0);
                 est_f = (float)((double)ds - uni);
+                fx_ok = false;  // per-vertex sums take the double at both ends
+                V = 0ull;
+                big = (double)ds - uni;
+                if (K >= k) add_fixed52(rlo, rhi, uni);
             }
             if (p.aux) p.aux[e] = (int32_t)(K | (clit << 16));
             if (p.count) p.count[e] = (int32_t)((p.est == PG_EST_1H_LITERAL) ? clit : cun);
@@ -715,6 +748,21 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
         }
     }
 
+    if (want_hist && kmv) {
+        // exact 128-bit warp sum, then one 128-bit global add (carry from the low word)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long olo = __shfl_xor_sync(0xffffffffu, rlo, o);
+            const unsigned long long ohi = __shfl_xor_sync(0xffffffffu, rhi, o);
+            rlo += olo;
+            rhi += ohi + (rlo < olo);
+        }
+        if (lane == 0 && (rlo | rhi)) {
+            unsigned long long *acc = reinterpret_cast<unsigned long long *>(p.hist + 2 * hk2 + 2 * hk);
+            const unsigned long long old = atomicAdd(acc, rlo);
+            atomicAdd(acc + 1, rhi + (old + rlo < old ? 1ull : 0ull));
+        }
+    }
     if (want_hist) {
         __syncthreads();
         for (int i = threadIdx.x; i < hk2; i += blockDim.x) {
@@ -801,6 +849,23 @@ __device__ __forceinline__ void tc_dot_block(const uint64_t *__restrict__ hist, 
             main_ += (double)hd * ((double)c / (double)(k + c));
             edges += h;
             sum += h * c;
+        }
+    } else if (est == PG_EST_1H_KMV) {
+        // sum of d_u + d_v over all edges, minus the exact union sizes K of the edges whose union
+        // sketch has fewer than k values, minus the 128-bit sum of the others' real estimates;
+        // alt: the c_union / K estimate of the same edges
+        const uint32_t hk2 = hk * hk;
+        for (uint32_t i = threadIdx.x; i < hk2; i += blockDim.x) {
+            const uint32_t K = i / hk, c = i % hk;
+            const unsigned long long h = hist[i], hd = hist[hk2 + i];
+            main_ += (double)hd - (K < k ? (double)h * (double)K : 0.0);
+            alt += (double)hd * ((K + c) > 0 ? (double)c / (double)(K + c) : 0.0);
+            edges += h;
+            sum += h * c;
+        }
+        if (threadIdx.x == 0) {
+            const unsigned long long rlo = hist[2 * hk2 + 2 * hk], rhi = hist[2 * hk2 + 2 * hk + 1];
+            main_ -= (double)rhi * 0x1p12 + (double)rlo * 0x1p-52;
         }
     } else {
         const uint32_t hk2 = hk * hk;
@@ -933,7 +998,8 @@ int pow2_at_least(int x) {
 int64_t hist_bins(int32_t kind, uint32_t l, uint32_t k, int32_t estimator) {
     if (kind == BLOOM) return (int64_t)l + 1 + (estimator == PG_EST_BF_OR ? 1 : 0);
     if (kind == KHASH) return 2 * ((int64_t)k + 1);
-    if (kind == ONEHASH) return 2 * ((int64_t)k + 1) * (k + 1) + 2 * ((int64_t)k + 1);
+    if (kind == ONEHASH)
+        return 2 * ((int64_t)k + 1) * (k + 1) + 2 * ((int64_t)k + 1) + (estimator == PG_EST_1H_KMV ? 2 : 0);
     return 0;
 }
 

@@ -73,7 +73,6 @@ extern "C" pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *inde
                "pg_triangle_count_noalloc: the exact estimator needs scratch proportional to the "
                "graph; use pg_triangle_count with a workspace");
     st = check_estimator(sk, estimator);
-    if (st == PG_OK) st = check_totals(estimator, "pg_triangle_count_noalloc");
     if (st) return st;
     st = check_sketch(g, sk);
     if (st) return st;

@@ -106,14 +106,11 @@ def test_argument_errors_return_codes(L):
     # unknown estimator
     assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk), 42,
                                ctypes.c_void_p(0x7000), need, out, None) == -1
-    # KMV (per-edge and per-pair outputs only) in a call that reduces totals
-    sk1 = pg.SketchDesc(pg.SK_1HASH, 0, 0, 16, 1, 4, 64, 0x3000)
-    need1 = L.pg_workspace_bytes(byref(g), byref(sk1), pg.EST_1H_KMV)
-    assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk1), pg.EST_1H_KMV,
-                               ctypes.c_void_p(0x7000), need1, out, None) == -9
-    assert b"KMV" in L.pg_last_error()
+    # KMV reads 1-Hash rows; its totals need two more histogram bins than 1-Hash
     assert L.pg_triangle_count(byref(g), ctypes.c_void_p(0x6000), byref(sk), pg.EST_1H_KMV,
-                               ctypes.c_void_p(0x7000), need, out, None) == -1  # needs a 1-Hash sketch
+                               ctypes.c_void_p(0x7000), need, out, None) == -1
+    sk1 = pg.SketchDesc(pg.SK_1HASH, 0, 0, 16, 1, 4, 64, 0x3000)
+    assert L.pg_hist_bins(byref(sk1), pg.EST_1H_KMV) == L.pg_hist_bins(byref(sk1), pg.EST_1H) + 2
     # odd pairs pointer
     assert L.pg_jaccard_pairs(byref(g), None, byref(sk), pg.EST_KH, ctypes.c_void_p(0x8004), 3,
                               ctypes.c_void_p(0x7000), need, None, None, None) == -1

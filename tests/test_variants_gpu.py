@@ -141,8 +141,9 @@ def test_variant_pairs_match_edges(pg):
 
 @pytest.mark.parametrize("name", ["er4096", "rmat12", "hubs"])
 def test_kmv_upper_edges(pg, name):
-    """KMV (Sec. IX) on the 1-Hash rows over every upper edge (pairs = NULL),
-    against the oracle; the calls that reduce estimates into totals refuse it."""
+    """KMV (Sec. IX) on the 1-Hash rows over every upper edge (pairs = NULL) and
+    its totals (TC from the 1-Hash histograms and the exact 128-bit sum of the
+    real union estimates; per-vertex triangles and LCC), against the oracle."""
     rp, cl = _graph(name)
     g = pg.graph(torch.from_numpy(rp).cuda(), torch.from_numpy(cl).cuda())
     k = 16
@@ -157,7 +158,11 @@ def test_kmv_upper_edges(pg, name):
     _close(jac.cpu().numpy(), want["jac"], RTOL_F32, 1e-5)
     c, a, _ = pg.edge_counts(g, sk, pg.EST_1H_KMV, None, want_aux=True)
     np.testing.assert_array_equal(c.cpu().numpy(), counts["count"])
-    for call in (lambda: pg.triangle_count(g, sk, pg.EST_1H_KMV), lambda: pg.clustering(g, sk, pg.EST_1H_KMV)):
-        with pytest.raises(pg.PGError) as ei:
-            call()
-        assert ei.value.status == -9
+    ref = O.analyze(rp, cl, O.EST_1H_KMV, k=k, seed=3, sk=osk)
+    tc = pg.triangle_count(g, sk, pg.EST_1H_KMV)
+    assert tc["edges"] == ref["m"] and tc["count_sum"] == int(np.sum(counts["count"]))
+    assert tc["est_tc"] == pytest.approx(ref["tc"], rel=RTOL_F64, abs=1e-6)
+    lcc, tri, tc2 = pg.clustering(g, sk, pg.EST_1H_KMV)
+    assert pg.read_tc_result(tc2)["est_tc"] == tc["est_tc"]  # the 128-bit sum does not depend on order
+    _close(tri.cpu().numpy(), ref["T"], RTOL_F64, 1e-6)
+    _close(lcc.cpu().numpy(), ref["lcc"], RTOL_F32, 1e-6)
