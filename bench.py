@@ -1117,10 +1117,21 @@ def run_reference(args):
         rates.append(r)
         secs += dt
     value = float(np.median(rates))
+    # the same config keys as our arm's line
+    rp_h, cl_h = rp.cpu().numpy(), cl.cpu().numpy()
+    n = int(rp_h.size - 1)
+    m = int(np.count_nonzero(cl_h > np.repeat(np.arange(n), np.diff(rp_h))))
+    passes = ["bloom"] + ["bloom_" + nm for nm in cfg.get("bloom_variants", ())]
+    passes += ["khash"] if cfg["khash"] else []
+    passes += (["onehash"] + ["onehash_" + nm for nm in cfg.get("onehash_variants", ())]) if cfg["onehash"] else []
+    config = {"workload": args.workload, "n": n, "nnz": int(cl_h.size), "m": m, "bloom_bits": bits,
+              "bloom_b": cfg["b"], "khash_k": cfg["khash"], "onehash_k": cfg["onehash"],
+              "per_edge_jaccard": cfg["jaccard"], "passes": passes,
+              "l2": "a bounded sample on the host cores", "parallelism": "rank 0 only"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-            "data": "synthetic", "config": {"workload": args.workload, "bloom_bits": bits},
+            "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
