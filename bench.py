@@ -1139,7 +1139,7 @@ def run_reference(args):
 
 
 def run_reference_batch(args, ws, dev):
-    parts, cfg, _, _, _ = generate_batch(args.workload, dev)
+    parts, cfg, rp_u, cl_u, _ = generate_batch(args.workload, dev)
     per_step = 4.0 * max(1, 60 // max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
         oracle_batch_sample(parts, cfg, target_s=min(per_step, 5.0), seed=1)
@@ -1149,10 +1149,17 @@ def run_reference_batch(args, ws, dev):
         rates.append(r)
         secs += dt
     value = float(np.median(rates))
+    buckets = {}
+    for c in cfg:
+        buckets.setdefault(f"{c[0]}b{c[1]}", {"graphs": 0})["graphs"] += 1
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "intersections/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
-            "data": "synthetic", "config": {"workload": args.workload, "graphs": len(parts)},
+            "data": "synthetic",
+            "config": {"workload": args.workload, "graphs": len(parts), "n": int(rp_u.numel() - 1),
+                       "nnz": int(cl_u.numel()), "m": int(cl_u.numel()) // 2,
+                       "budget": WORKLOADS[args.workload]["budget"], "buckets": buckets,
+                       "l2": "a bounded sample on the host cores", "parallelism": "rank 0 only"},
             "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
