@@ -24,6 +24,7 @@ import argparse
 import ctypes
 import hashlib
 import json
+import math
 import os
 import re
 import struct
@@ -379,6 +380,37 @@ def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     h2d = host_rp.numel() * 4 + host_col.numel() * 4
     d2h_bytes = sum(h.numel() * h.element_size() for _, h in d2h)
     return start.elapsed_time(end) / steps, wall, h2d, d2h_bytes
+
+
+def tc_deviation_bounds(row_ptr, passes, delta: float = 0.05) -> dict:
+    """Thm. 7.1: the deviation t with P(|TC - TC^| >= t) <= delta, per pass.
+    Bloom AND (when b * max degree <= 0.499 l log l; the (1 + o(1)) factor
+    dropped): t = sqrt(2 m^2 C / (9 delta)), C the MSE bound of Prop. 4.1 at
+    the maximum degree; 1-Hash / k-Hash: the smaller t of the two Hoeffding
+    forms, (sum d^2) sqrt(ln(2/delta) / (18 k)) and sqrt(4 (max d + 1)
+    (sum d^3) ln(2/delta) / (9 k)). passes: (name, kind, l, b, k) tuples;
+    None for estimators the theorem does not cover."""
+    rp = np.asarray(row_ptr.cpu().numpy() if hasattr(row_ptr, "cpu") else row_ptr, dtype=np.int64)
+    d = np.diff(rp).astype(np.float64)
+    m = float(d.sum()) / 2.0
+    dmax = float(d.max()) if d.size else 0.0
+    s2, s3 = float(np.sum(d * d)), float(np.sum(d * d * d))
+    lg = math.log(2.0 / delta)
+    out = {}
+    for name, kind, l, b, k in passes:
+        if kind == "bloom_and":
+            if b * dmax > 0.499 * l * math.log(l):
+                out[name] = {"t": None, "reason": "b * max degree > 0.499 l log l: the bound does not apply"}
+                continue
+            C = math.exp(dmax * b / (l - 1)) * l / b**2 - l / b**2 - dmax / b
+            out[name] = {"t": math.sqrt(2.0 * m * m * max(C, 0.0) / (9.0 * delta))}
+        elif kind == "minhash":
+            t1 = s2 * math.sqrt(lg / (18.0 * k))
+            t2 = math.sqrt(4.0 * (dmax + 1.0) * s3 * lg / (9.0 * k))
+            out[name] = {"t": min(t1, t2)}
+        else:
+            out[name] = None
+    return out
 
 
 def exact_comparison(pipe: Pipeline):
@@ -1235,6 +1267,20 @@ def main():
                for nm, r in res.items()}
         exact = {"ms": ex_ms, "exact_tc": ex["exact_tc"], "edges_per_s": pipe.m / (ex_ms * 1e-3),
                  "tc_rel_error": rel}
+        # Thm. 7.1's 95% deviation radius beside the measured error (relative to the exact count)
+        try:
+            kinds = []
+            for nm, sk, est in pipe.passes:
+                kind = ("bloom_and" if est == pg.EST_BF_AND else
+                        "minhash" if est in (pg.EST_KH, pg.EST_1H) else None)
+                kinds.append((nm, kind, sk.bits, sk.b, sk.k))
+            bounds = tc_deviation_bounds(rp, kinds)
+            exact["thm71_radius_95"] = {
+                nm: (None if v is None else dict(v, rel=(v["t"] / ex["exact_tc"]
+                                                         if v.get("t") is not None and ex["exact_tc"] else None)))
+                for nm, v in bounds.items()}
+        except Exception as err:  # a report beside the measurement: never fail the bench line
+            exact["thm71_radius_95"] = {"error": repr(err)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

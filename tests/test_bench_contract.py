@@ -6,6 +6,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CONTRACT = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
             "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline", "impl"}
@@ -26,3 +28,30 @@ def test_reference_line_keys():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["value"] > 0 and line["higher_is_better"] is True
+
+
+def test_thm71_radius():
+    """Thm. 7.1's 95% deviation radius as the bench reports it: MinHash from the
+    degree sums (the smaller of the two Hoeffding forms, each of which gives
+    exactly delta back), Bloom AND only under the theorem's condition."""
+    import math
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2208_11469_gb300 import synth
+    rp, cl = synth.erdos_renyi(4096, 16.0, seed=1)
+    d = np.diff(rp.numpy()).astype(np.float64)
+    k, delta = 32, 0.05
+    out = bench.tc_deviation_bounds(rp, [("kh", "minhash", 0, 0, k), ("bf", "bloom_and", 1024, 1, 0),
+                                         ("bf_small", "bloom_and", 64, 16, 0), ("x", None, 0, 0, 0)], delta)
+    t = out["kh"]["t"]
+    p1 = 2 * math.exp(-18 * k * t * t / (np.sum(d * d) ** 2))
+    p2 = 2 * math.exp(-9 * k * t * t / (4 * (d.max() + 1) * np.sum(d ** 3)))
+    assert min(p1, p2) <= delta * (1 + 1e-9) and max(p1, p2) >= delta * (1 - 1e-9)
+    m = d.sum() / 2
+    b, l, dm = 1, 1024, d.max()
+    C = math.exp(dm * b / (l - 1)) * l / b**2 - l / b**2 - dm / b
+    tb = out["bf"]["t"]
+    assert 2 * m * m * C / (9 * tb * tb) == pytest.approx(delta, rel=1e-12)
+    assert out["bf_small"]["t"] is None and "0.499" in out["bf_small"]["reason"]  # 16 * max d > 0.499 * 64 ln 64
+    assert out["x"] is None
