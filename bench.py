@@ -1149,14 +1149,13 @@ def run_reference(args):
         rates.append(r)
         secs += dt
     value = float(np.median(rates))
-    # the same config keys as our arm's line
-    rp_h, cl_h = rp.cpu().numpy(), cl.cpu().numpy()
-    n = int(rp_h.size - 1)
-    m = int(np.count_nonzero(cl_h > np.repeat(np.arange(n), np.diff(rp_h))))
+    # the same config keys as our arm's line (the generated graphs are simple and symmetric: m = nnz / 2)
+    n = int(rp.numel() - 1)
+    m = int(cl.numel()) // 2
     passes = ["bloom"] + ["bloom_" + nm for nm in cfg.get("bloom_variants", ())]
     passes += ["khash"] if cfg["khash"] else []
     passes += (["onehash"] + ["onehash_" + nm for nm in cfg.get("onehash_variants", ())]) if cfg["onehash"] else []
-    config = {"workload": args.workload, "n": n, "nnz": int(cl_h.size), "m": m, "bloom_bits": bits,
+    config = {"workload": args.workload, "n": n, "nnz": int(cl.numel()), "m": m, "bloom_bits": bits,
               "bloom_b": cfg["b"], "khash_k": cfg["khash"], "onehash_k": cfg["onehash"],
               "per_edge_jaccard": cfg["jaccard"], "passes": passes,
               "l2": "a bounded sample on the host cores", "parallelism": "rank 0 only"}
