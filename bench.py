@@ -42,7 +42,7 @@ import torch  # noqa: E402
 
 METRIC = "sketched edge intersections/s"
 
-# workload -> generator + sketch configuration (BASELINE configs)
+# workload -> generator + sketch configuration
 WORKLOADS = {
     # R-MAT scale 24, edge factor 32, Bloom at 25% of CSR bytes (b = 2), k-Hash k = 64, exact comparison
     "rmat24": dict(gen=("rmat", 24, 32, 24), budget=0.25, b=2, khash=64, onehash=None, jaccard=False),
@@ -311,7 +311,7 @@ class Pipeline:
 
 
 def algorithmic_bytes(pipe: Pipeline, name: str) -> float:
-    """Algorithmic DRAM bytes of one fused intersection pass (see DESIGN.md):
+    """Algorithmic DRAM bytes of one fused intersection pass:
     per undirected edge the gathered neighbour sketch row (payload bytes) plus
     its CSR entry and the two row offsets of v (degree) for MinHash; per vertex
     its own sketch row, its two row offsets and upper offset, and the outputs

@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path, called through the C ABI, against the CPU
 oracle on the same seeded graphs.
 
-Bar (BASELINE's stated tolerances): bit-exact sketches, per-edge integer
+Bar: bit-exact sketches, per-edge integer
 counts and histograms; 1e-5 relative on per-edge float32 estimates,
 Jaccard and LCC; 1e-9 relative on double totals and per-vertex triangles."""
 import numpy as np
