@@ -4,7 +4,7 @@
  * Method: Besta et al., "ProbGraph: High-Performance and High-Accuracy Graph
  * Mining with Probabilistic Set Representations", SC'22 (arXiv 2208.11469).
  * Each vertex neighbourhood N_v gets a fixed-size sketch (Bloom filter,
- * k-Hash MinHash or 1-Hash MinHash, Sec. II-C); |N_u ∩ N_v| is estimated
+ * k-Hash MinHash or 1-Hash MinHash, Sec. II-D); |N_u ∩ N_v| is estimated
  * per edge from the two sketches (Sec. IV) and the estimates are reduced
  * into the triangle count (Sec. VII), per-vertex local clustering
  * coefficients and per-edge / per-pair Jaccard and common-neighbour scores
@@ -120,9 +120,9 @@ pg_status pg_build_edge_index(const pg_csr *g, void *index, size_t index_bytes,
 const int32_t *pg_edge_index_upper_off(const void *index);
 
 /* ----------------------------------------------------------------- sketches */
-#define PG_SK_BLOOM 1 /* Bloom filter, Sec. II-C */
-#define PG_SK_KHASH 2 /* MinHash, k-Hash variant, Sec. II-C */
-#define PG_SK_1HASH 3 /* MinHash, 1-Hash variant, Sec. II-C */
+#define PG_SK_BLOOM 1 /* Bloom filter, Sec. II-D */
+#define PG_SK_KHASH 2 /* MinHash, k-Hash variant, Sec. II-D */
+#define PG_SK_1HASH 3 /* MinHash, 1-Hash variant, Sec. II-D */
 
 /* One sketch per vertex, row-major, row v at data + v * stride_bytes.
  *   Bloom: bits l (multiple of 64, 64..1024) in 64-bit words, bit p of the
@@ -133,7 +133,7 @@ const int32_t *pg_edge_index_upper_off(const void *index);
  *   1-Hash: k uint32 (1..32): the min(k, d_v) smallest values of h_0 over
  *          N_v in increasing order, then 0xFFFFFFFF padding. Because every
  *          h_i is a bijection on 32-bit ids, storing hash values is
- *          equivalent to storing the minimising elements of Sec. II-C. */
+ *          equivalent to storing the minimising elements of Sec. II-D. */
 typedef struct pg_sketch {
     int32_t kind;         /* PG_SK_* */
     uint32_t bits;        /* Bloom: l */
@@ -155,7 +155,7 @@ uint32_t pg_bloom_bits_for_budget(double s, int32_t n, int64_t nnz);
  * too long for one warp, which are finished by a second kernel). */
 size_t pg_build_workspace_bytes(const pg_csr *g);
 
-/* Bloom filter construction (Sec. II-C): for every v, start from l zero bits
+/* Bloom filter construction (Sec. II-D): for every v, start from l zero bits
  * and, for each x in N_v and i < b, set bit floor(h_i(x) * l / 2^32).
  * sk: kind = PG_SK_BLOOM with bits, b, seed, n, stride_bytes, data set.
  * workspace: DEVICE, >= pg_build_workspace_bytes(g), 16-byte aligned.
@@ -163,7 +163,7 @@ size_t pg_build_workspace_bytes(const pg_csr *g);
 pg_status pg_build_bloom(const pg_csr *g, const pg_sketch *sk, void *workspace,
                          size_t workspace_bytes, pg_stream_t stream);
 
-/* MinHash construction (Sec. II-C), kind PG_SK_KHASH or PG_SK_1HASH, with
+/* MinHash construction (Sec. II-D), kind PG_SK_KHASH or PG_SK_1HASH, with
  * k, seed, n, stride_bytes, data set. Overwrites the first k entries of
  * every row of sk->data (row padding beyond k entries is not written).
  * workspace as for pg_build_bloom. */
@@ -175,7 +175,7 @@ pg_status pg_build_minhash(const pg_csr *g, const pg_sketch *sk, void *workspace
  * copied first, then col in chunks of whole rows (about chunk_entries
  * entries each, at least one row) on copy_stream; after each chunk, stream
  * waits for it and builds every sketch's rows of that chunk (the builds of
- * Sec. II-C are per row, so the result equals pg_build_bloom /
+ * Sec. II-D are per row, so the result equals pg_build_bloom /
  * pg_build_minhash on the uploaded CSR). The copies start after the work
  * already enqueued on stream, so a previous step that reads g is not
  * overwritten. When the call returns, stream is ordered after the whole
@@ -351,7 +351,7 @@ pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *index, const pg
                                     int32_t estimator, pg_tc_result *out, pg_stream_t stream);
 
 /* ----------------------------------------------------- Jarvis-Patrick --
- * Jarvis-Patrick clustering (Sec. III-B, Listing "Jarvis-Patrick
+ * Jarvis-Patrick clustering (Sec. III, Listing "Jarvis-Patrick
  * clustering"): the edges (u, v) whose common-neighbour count |N_u ∩ N_v|
  * exceeds tau form the clustering C; the clusters are the connected
  * components of (V, C), singletons included. The count is exact
@@ -401,7 +401,7 @@ pg_status pg_clique4_count(const pg_csr *g, int32_t estimator, uint32_t bits, ui
 
 /* ---------------------------------------------------------------- batch --
  * Many small graphs analysed together (the per-graph Bloom-filter triangle
- * count of Sec. V, Eq. bf_int, and the LCC of Sec. II-B, per graph), in one
+ * count of Sec. V, Eq. bf_int, and the LCC of Sec. III-A, per graph), in one
  * launch sequence that is captured once as a CUDA graph and replayed.
  *
  * The G graphs come as ONE block-diagonal CSR g with global vertex ids: graph

@@ -6,7 +6,7 @@ CPU-baseline leg may import this module. It never imports the CUDA library
 and the CUDA library never imports it.
 
 Every function restates one passage of Besta et al., SC'22 (ProbGraph):
-  * sketches:   Sec. II-C (Bloom filter, k-Hash, 1-Hash)
+  * sketches:   Sec. II-D (Bloom filter, k-Hash, 1-Hash)
   * estimators: Eq. (est_ss_bf), Eq. (bf_int), Eq. (limit_xs),
                 Eq. (est_int_mh), Sec. IV-D and the KMV estimator of
                 Sec. IX (est_kmv)
@@ -127,7 +127,7 @@ def hash_array(seed: int, i: int, x) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# sketches (Sec. II-C)
+# sketches (Sec. II-D)
 # --------------------------------------------------------------------------
 
 def bloom_bits(row_ptr, col, l: int, b: int, seed: int) -> np.ndarray:
@@ -489,7 +489,7 @@ def analyze(row_ptr, col, est: int, *, l=256, b=2, k=16, seed=1, sk=None):
 
 
 # --------------------------------------------------------------------------
-# Jarvis-Patrick clustering (Sec. III-B, Listing "Jarvis-Patrick clustering")
+# Jarvis-Patrick clustering (Sec. III, Listing "Jarvis-Patrick clustering")
 # --------------------------------------------------------------------------
 
 def components(n: int, eu, ev, keep) -> np.ndarray:

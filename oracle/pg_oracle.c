@@ -15,7 +15,7 @@
  *   - Bloom filters are kept one BYTE per bit (0/1) so that every bit can be
  *     read directly; pgo_bloom_pack only re-lays them out as 64-bit words
  *     (bit p -> word p/64, bit p%64) for comparison with packed filters.
- *   - MinHash sketches hold ELEMENTS (vertex ids), as M_X does in Sec. II-C;
+ *   - MinHash sketches hold ELEMENTS (vertex ids), as M_X does in Sec. II-D;
  *     -1 marks an empty slot.
  *   - This file computes sketches and integer counts only; the estimators
  *     (double precision) are written out in oracle.py.
@@ -70,7 +70,7 @@ uint32_t pgo_bit_position(uint32_t h, uint32_t l)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Bloom filters (Sec. II-C "Bloom filters").                               */
+/* Bloom filters (Sec. II-D "Bloom filters").                               */
 /* ------------------------------------------------------------------------ */
 
 /* Construct B_X for every vertex neighbourhood X = N_v: start from l zero
@@ -138,7 +138,7 @@ int32_t pgo_bloom_ones(const uint8_t *BX, uint32_t l)
 }
 
 /* ------------------------------------------------------------------------ */
-/* MinHash, k-Hash variant (Sec. II-C; estimator Sec. IV-C, reading D).      */
+/* MinHash, k-Hash variant (Sec. II-D; estimator Sec. IV-C, reading D).      */
 /* ------------------------------------------------------------------------ */
 
 /* M_X = {x_{1,min}, ..., x_{k,min}}: for each hash function i separately the
@@ -170,7 +170,7 @@ int32_t pgo_khash_matches(const int32_t *MX, const int32_t *MY, int32_t k)
 }
 
 /* ------------------------------------------------------------------------ */
-/* MinHash, 1-Hash variant (Sec. II-C; estimator Sec. IV-D, reading C).      */
+/* MinHash, 1-Hash variant (Sec. II-D; estimator Sec. IV-D, reading C).      */
 /* ------------------------------------------------------------------------ */
 
 static uint32_t g_sort_seed; /* qsort comparator context (serial oracle) */
@@ -335,7 +335,7 @@ void pgo_hash_array(uint32_t seed, uint32_t i, const int32_t *x, int64_t cnt, ui
 
 /* ------------------------------------------------------------------------ */
 /* Connected components of a subset of the edges (Jarvis-Patrick clustering,  */
-/* Sec. III-B, Listing "Jarvis-Patrick clustering": the clusters are the      */
+/* Sec. III, Listing "Jarvis-Patrick clustering": the clusters are the      */
 /* connected components of (V, C), C = edges whose |N_u ∩ N_v| exceeds tau).  */
 /* ------------------------------------------------------------------------ */
 

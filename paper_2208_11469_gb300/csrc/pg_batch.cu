@@ -252,7 +252,7 @@ cudaError_t run_pull(const PullParams &p, cudaStream_t s) {
 // from the search over the row ends), and stores the 32 filters with one
 // coalesced row store per lane. Every graph hashes its own ids (global id
 // minus the graph's first id) with the bucket's b hash functions, so the
-// filter bits are those of the single-graph build (Sec. II-B: bit
+// filter bits are those of the single-graph build (Sec. II-D: bit
 // floor(h_i(x) l / 2^32) for each element x and i < b); OR does not depend
 // on the order in which entries are hashed.
 struct BuildParams {

@@ -1,4 +1,4 @@
-// Jarvis-Patrick clustering (Sec. III-B, Listing "Jarvis-Patrick
+// Jarvis-Patrick clustering (Sec. III, Listing "Jarvis-Patrick
 // clustering"): an edge (u, v) stays in the clustering C when its
 // common-neighbour count |N_u ∩ N_v| (exact or estimated) exceeds tau; the
 // clusters are the connected components of (V, C).

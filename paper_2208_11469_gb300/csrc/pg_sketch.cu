@@ -1,4 +1,4 @@
-// Sketch construction kernels (Sec. II-C): Bloom filters, k-Hash and 1-Hash
+// Sketch construction kernels (Sec. II-D): Bloom filters, k-Hash and 1-Hash
 // MinHash of every neighbourhood N_v.
 //
 // Work mapping. One warp builds one vertex's sketch when d_v is at most a

@@ -1,4 +1,4 @@
-"""Pins of the oracle's Jarvis-Patrick clustering (Sec. III-B, Listing
+"""Pins of the oracle's Jarvis-Patrick clustering (Sec. III, Listing
 "Jarvis-Patrick clustering"): clusters are the connected components of the
 graph restricted to the edges whose |N_u ∩ N_v| exceeds tau.
 
