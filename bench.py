@@ -196,19 +196,44 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# int32 ALU-pipe lane operations per SM per clock (16 lanes in each of the
+# four SM sub-partitions), the rate of integer add / logical / shift / min.
+ALU_OPS_PER_SM_CLOCK = 64
+# ALU-pipe operations per k-Hash hash evaluation in the builders' source: one
+# XOR with the seed's pre-image, two shift + XOR pairs and one min (the two
+# multiplies run on the multiply-add pipe).
+ALU_OPS_PER_HASH = 6
+
+
+def alu_peak(sm_mhz):
+    """Integer ALU-pipe peak of this GPU at the sampled SM clock (ops/s)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return sms * ALU_OPS_PER_SM_CLOCK * float(sm_mhz) * 1e6, sms
+
+
+# The sources a pass's DRAM traffic depends on: the pass kernels, the shared
+# device code and the edge index (whose list order decides the L2 reuse).
+PASS_SOURCES = ("pg_intersect.cu", "pg_internal.cuh", "pg_index.cu")
+
+
+def source_fingerprint() -> str:
+    """sha256 over the pass sources, in PASS_SOURCES order."""
+    h = hashlib.sha256()
+    for f in PASS_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2208_11469_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(name: str):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel
-    source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch from a committed ncu summary, if the pass
+    sources are unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", txt)
-    if not m or not h:
-        return None
-    src = os.path.join(ROOT, "paper_2208_11469_gb300", "csrc", "pg_intersect.cu")
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+    if not m or not h or source_fingerprint() != h.group(1):
         return None
     return float(m.group(1))
 
@@ -430,71 +455,235 @@ def exact_comparison(pipe: Pipeline):
 
 
 # ------------------------------------------------------- CPU oracle leg
-def oracle_sample(row_ptr_d, col_d, pipe_cfg, bits, target_s=15.0, seed=0):
-    """Times the oracle on a bounded sample of the workload: a seeded random
-    set of upper edges; the oracle builds the sketches of every endpoint row
-    it needs and intersects the sampled edges, as the GPU step does for all
-    of them. Returns (rate, seconds, edges, description)."""
+def oracle_passes(cfg, bits):
+    """The passes of the workload's step as the oracle's pass descriptors."""
     from oracle import oracle as O
-    rp = row_ptr_d.cpu().numpy().astype(np.int64)
-    n = rp.size - 1
-    gen = np.random.default_rng(seed)
+    out = [dict(name="bloom", est=O.EST_BF_AND, l=bits, b=cfg["b"], k=0)]
+    for nm in cfg.get("bloom_variants", ()):
+        out.append(dict(name="bloom_" + nm, est={"or": O.EST_BF_OR, "ss": O.EST_BF_SS, "l": O.EST_BF_L}[nm],
+                        l=bits, b=cfg["b"], k=0))
+    if cfg.get("khash"):
+        out.append(dict(name="khash", est=O.EST_KH, l=0, b=0, k=cfg["khash"]))
+    if cfg.get("onehash"):
+        out.append(dict(name="onehash", est=O.EST_1H, l=0, b=0, k=cfg["onehash"]))
+        for nm in cfg.get("onehash_variants", ()):
+            out.append(dict(name="onehash_" + nm, est={"kmv": O.EST_1H_KMV}[nm], l=0, b=0, k=cfg["onehash"]))
+    return out
 
-    def run(E):
-        # sample upper edges uniformly: draw CSR entries, keep those with v > u
-        j = gen.integers(0, rp[-1], size=4 * E + 16)
-        u = np.searchsorted(rp, j, side="right") - 1
-        v = col_d[torch.from_numpy(j).to(col_d.device)].cpu().numpy().astype(np.int64)
-        keep = v > u
-        u, v = u[keep][:E], v[keep][:E]
-        verts = np.unique(np.concatenate([u, v]))
-        # sub-CSR of the needed rows (a sketch depends only on its own row)
-        starts, ends = rp[verts], rp[verts + 1]
-        lens = ends - starts
-        sub_rp = np.zeros(verts.size + 1, np.int64)
-        sub_rp[1:] = np.cumsum(lens)
-        idx = np.repeat(starts - sub_rp[:-1], lens) + np.arange(int(sub_rp[-1]), dtype=np.int64)
-        sub_col = col_d[torch.from_numpy(idx).to(col_d.device)].cpu().numpy().astype(np.int32)
-        su = np.searchsorted(verts, u).astype(np.int32)
-        sv = np.searchsorted(verts, v).astype(np.int32)
-        sub_rp32 = sub_rp.astype(np.int32)
-        deg = lens
-        t0 = time.perf_counter()
-        bf = O.bloom_bits(sub_rp32, sub_col, bits, pipe_cfg["b"], 1)
-        c = O.bloom_pairs(bf, su, sv)
-        est = O.est_and(c, bits, pipe_cfg["b"])
-        tot = float(est.sum())
-        npass = 1
-        if pipe_cfg.get("khash"):
-            k = pipe_cfg["khash"]
-            M = O.khash(sub_rp32, sub_col, k, 1)
-            c2 = O.khash_pairs(M, su, sv)
-            tot += float(O.est_minhash(c2, np.full(c2.size, k), deg[su], deg[sv]).sum())
-            npass += 1
-        if pipe_cfg.get("onehash"):
-            k = pipe_cfg["onehash"]
-            M1 = O.onehash(sub_rp32, sub_col, k, 1)
-            cnt = O.pair_counts(sub_rp32, sub_col, O.EST_1H, M1, su, sv, seed=1)
-            tot += float(O.pair_estimates(sub_rp32, O.EST_1H, cnt, su, sv, k=k).sum())
-            npass += 1
-            for nm in pipe_cfg.get("onehash_variants", ()):
-                est_v = {"kmv": O.EST_1H_KMV}[nm]
-                cnt = O.pair_counts(sub_rp32, sub_col, est_v, M1, su, sv, seed=1)
-                tot += float(O.pair_estimates(sub_rp32, est_v, cnt, su, sv, k=k).sum())
-                npass += 1
-        dt = time.perf_counter() - t0
-        return dt, u.size, npass, verts.size, int(lens.sum())
 
-    E = 2000
-    dt, e, npass, nv, nz = run(E)
-    for _ in range(4):
-        if dt >= target_s * 0.5:
-            break
-        E = int(min(E * max(2.0, target_s / max(dt, 1e-3)), 5_000_000))
-        dt, e, npass, nv, nz = run(E)
-    desc = (f"{e} uniformly sampled upper edges ({nv} endpoint rows, {nz} CSR entries): oracle sketches of "
-            f"those rows + {npass} sketched intersections per edge, serial C/numpy on 1 host core")
-    return npass * e / dt, dt, e, desc
+def host_sub_csr(rp, col_d, rows):
+    """The rows `rows` (host int64 ids) of the device CSR as a host sub-CSR
+    whose entries keep the graph's neighbour ids (a sketch row depends only on
+    its own row, so its sketch equals the whole graph's)."""
+    starts = rp[rows]
+    lens = rp[rows + 1] - starts
+    sub_rp = np.zeros(rows.size + 1, np.int64)
+    sub_rp[1:] = np.cumsum(lens)
+    idx = np.repeat(starts - sub_rp[:-1], lens) + np.arange(int(sub_rp[-1]), dtype=np.int64)
+    sub_col = col_d[torch.from_numpy(idx).to(col_d.device)].cpu().numpy().astype(np.int32)
+    return sub_rp.astype(np.int32), sub_col
+
+
+class OracleLeg:
+    """The CPU oracle timed on a bounded sample of the workload, extrapolated
+    to the whole graph.
+
+    Every phase of the oracle is per row (sketch builds, Sec. II-D) or per
+    edge (counts, estimates, totals and per-vertex sums, Sec. IV and VII), so
+    the whole-graph time is
+        T = t_build(R sampled rows) * n / R + t_pass(E sampled pairs) * m / E
+    with the rows drawn uniformly (an unbiased estimate of the whole build)
+    and each pair's endpoints drawn with probability proportional to degree,
+    as the endpoints of a uniformly drawn edge are, from a table of copies of
+    the sampled rows as large as the whole graph's sketch tables (at most
+    TABLE_BYTES per process), so that the pass misses the CPU caches as a
+    whole-graph pass does. The serial leg runs the chunks one after another
+    on one core; the all-core leg runs one chunk per core, each in its own
+    process, and its times are the slowest chunk's."""
+
+    TABLE_BYTES = 768 << 20
+
+    def __init__(self, row_ptr_d, col_d, cfg, bits, seed=0):
+        from oracle import oracle as O
+        O.build()
+        O.lib()
+        self.rp = row_ptr_d.cpu().numpy().astype(np.int64)
+        self.col_d = col_d
+        self.n = self.rp.size - 1
+        self.nnz = int(self.rp[-1])
+        self.m = self.nnz // 2  # simple symmetric generated graphs
+        self.passes = oracle_passes(cfg, bits)
+        from oracle import sample_timing as ST
+        keys = {ST.sketch_key(p) for p in self.passes}
+        # oracle row bytes: Bloom one byte per bit, MinHash k int32
+        self.row_bytes = sum(key[1] if key[0] == "bloom" else 4 * key[1] for key in keys)
+        self.rng = np.random.default_rng(seed)
+        self.order = self.rng.permutation(self.n)
+        self.next_row = 0
+        self.cores = max(1, os.cpu_count() or 1)
+        # calibration chunk: per-row build and per-pair pass costs
+        ch = self.chunks(min(self.n, 20000), 20000, 1)[0]
+        r = ST.time_chunk(ch["rp"], ch["cl"], self.passes, ch["pairs"], ch["table_rows"], pair_seed=ch["pair_seed"])
+        self.c_row = r["build_s"] / max(r["rows"], 1)
+        self.c_pair = r["pass_s"] / max(r["pairs"], 1)
+
+    def chunks(self, R, E, parts):
+        """parts chunks of R / parts fresh uniformly drawn rows each and
+        E / parts pairs each."""
+        out = []
+        table_rows = int(min(self.n, self.TABLE_BYTES // max(self.row_bytes, 1)))
+        for i in range(parts):
+            r = max(1, R // parts)
+            if self.next_row + r > self.n:
+                self.order = self.rng.permutation(self.n)
+                self.next_row = 0
+            rows = np.sort(self.order[self.next_row:self.next_row + r])
+            self.next_row += r
+            rp, cl = host_sub_csr(self.rp, self.col_d, rows)
+            out.append(dict(rp=rp, cl=cl, pairs=max(1, E // parts), table_rows=table_rows,
+                            pair_seed=int(self.rng.integers(1 << 31))))
+        return out
+
+    def sized(self, target_s, parts):
+        """Chunks sized for about target_s seconds of serial oracle work
+        (60% builds, 40% passes)."""
+        R = int(min(self.n, max(parts, 0.6 * target_s / max(self.c_row, 1e-12))))
+        E = int(min(5_000_000, max(1000 * parts, 0.4 * target_s / max(self.c_pair, 1e-12))))
+        return self.chunks(R, E, parts)
+
+    def _rate(self, build_s, pass_s, R, E):
+        T = build_s * self.n / R + pass_s * self.m / E
+        return len(self.passes) * self.m / T, T
+
+    def serial(self, chunks):
+        from oracle import sample_timing as ST
+        build = pss = 0.0
+        R = E = 0
+        for ch in chunks:
+            r = ST.time_chunk(ch["rp"], ch["cl"], self.passes, ch["pairs"], ch["table_rows"],
+                              pair_seed=ch["pair_seed"])
+            build += r["build_s"]
+            pss += r["pass_s"]
+            R += r["rows"]
+            E += r["pairs"]
+        rate, T = self._rate(build, pss, R, E)
+        return {"value": rate, "cores": 1, "rows": R, "pairs": E, "build_s": build, "pass_s": pss,
+                "whole_graph_s": T}
+
+    def parallel(self, chunks):
+        """One subprocess per chunk (plain `python -m oracle.sample_timing`,
+        no torch, no CUDA), all started together."""
+        import tempfile
+        with tempfile.TemporaryDirectory() as tmp:
+            procs = []
+            for i, ch in enumerate(chunks):
+                src = os.path.join(tmp, f"c{i}.npz")
+                np.savez(src, rp=ch["rp"], cl=ch["cl"], pairs=ch["pairs"], table_rows=ch["table_rows"], seed=1,
+                         pair_seed=ch["pair_seed"], passes=json.dumps(self.passes))
+                dst = os.path.join(tmp, f"r{i}.json")
+                env = dict(os.environ, PYTHONPATH=ROOT, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1")
+                procs.append((subprocess.Popen([sys.executable, "-m", "oracle.sample_timing", src, dst], cwd=ROOT,
+                                               env=env), dst))
+            res = []
+            for pr, dst in procs:
+                if pr.wait() != 0:
+                    raise RuntimeError("oracle timing subprocess failed")
+                with open(dst) as f:
+                    res.append(json.load(f))
+        R = sum(r["rows"] for r in res)
+        E = sum(r["pairs"] for r in res)
+        build = max(r["build_s"] for r in res)
+        pss = max(r["pass_s"] for r in res)
+        rate, T = self._rate(build, pss, R, E)
+        return {"value": rate, "cores": len(chunks), "rows": R, "pairs": E, "build_s": build, "pass_s": pss,
+                "whole_graph_s": T}
+
+    def describe(self, leg):
+        return (f"{leg['rows']} uniformly drawn rows (sketch builds) and {leg['pairs']} pairs with degree-weighted "
+                f"endpoints over tables of copies of those rows as large as the graph's (<= 768 MiB per process) "
+                f"({len(self.passes)} passes: counts, estimates, TC sum, per-vertex sums) of the "
+                f"n={self.n}, m={self.m} graph; whole-graph time = build * n/rows + pass * m/pairs "
+                f"= {leg['whole_graph_s']:.1f} s on {leg['cores']} core(s), oracle C/numpy unchanged, gcc -O3")
+
+
+def cpu_baseline(pipe_or_none, rp, cl, cfg, bits, serial_s=12.0):
+    """Both legs on the same sample: serial (1 core) and all host cores."""
+    leg = OracleLeg(rp, cl, cfg, bits, seed=0)
+    chunks = leg.sized(serial_s, leg.cores)
+    ser = leg.serial(chunks)
+    par = leg.parallel(chunks)
+    return {"value": par["value"], "unit": "intersections/s", "cores": par["cores"], "kind": "oracle",
+            "sample": leg.describe(par), "serial": dict(ser, sample=leg.describe(ser)),
+            "all_cores": par, "formula": "passes * m / (t_build * n / rows + t_pass * m / pairs)"}
+
+
+def parity_sample(pipe, seed=0, vertices=32, max_deg=16, hubs=8):
+    """Bit-exact check of the bench graph's own sketches and counts against the
+    oracle on a sample, after the timed steps: the sketch rows of `vertices`
+    random vertices of degree 2..max_deg, of all their neighbours and of the
+    `hubs` highest-degree vertices; the per-pair integer counts of every edge
+    at the sampled vertices and of every pair of hubs (pg_edge_counts); and
+    T_v and LCC of the sampled vertices from the step's own fused pass (1e-9
+    and 1e-5 relative)."""
+    from oracle import oracle as O
+    pg, g = pipe.pg, pipe.g
+    rp = g.row_ptr.cpu().numpy().astype(np.int64)
+    d = np.diff(rp)
+    rng = np.random.default_rng(seed)
+    cand = np.flatnonzero((d >= 2) & (d <= max_deg))
+    vs = np.sort(rng.choice(cand, size=min(vertices, cand.size), replace=False))
+    top = np.argsort(d)[::-1][:hubs]
+    nb_rp, nb_cl = host_sub_csr(rp, g.col, vs)
+    rows = np.unique(np.concatenate([vs, nb_cl.astype(np.int64), top]))
+    srp, scl = host_sub_csr(rp, g.col, rows)
+    loc = {int(v): i for i, v in enumerate(rows)}
+    # pairs: (v, u) for every neighbour u of a sampled v, then every pair of hubs
+    pu = np.repeat(vs, np.diff(nb_rp))
+    pv = nb_cl.astype(np.int64)
+    hu, hv = np.triu_indices(top.size, 1)
+    pu = np.concatenate([pu, top[hu]])
+    pv = np.concatenate([pv, top[hv]])
+    lu = np.array([loc[int(x)] for x in pu], np.int32)
+    lv = np.array([loc[int(x)] for x in pv], np.int32)
+    nv_pairs = int(nb_cl.size)
+    pairs_d = torch.from_numpy(np.stack([pu, pv], 1).astype(np.int32)).to(g.device)
+    out = {}
+    for name, sk, est in pipe.passes:
+        kw = dict(l=sk.bits, b=sk.b, k=sk.k)
+        rows_t = torch.from_numpy(rows).to(g.device)
+        if sk.kind == pg.SK_BLOOM:
+            osk = O.bloom_bits(srp, scl, sk.bits, sk.b, sk.seed)
+            words = sk.bits // 64
+            want = O.bloom_pack(osk, words)
+            got = sk.data.view(torch.int64).view(g.n, sk.stride // 8)[rows_t, :words].cpu().numpy().view(np.uint64)
+        elif sk.kind == pg.SK_KHASH:
+            osk = O.khash(srp, scl, sk.k, sk.seed)
+            want = O.khash_values(osk, sk.seed)
+            got = sk.data.view(torch.int32).view(g.n, sk.stride // 4)[rows_t, :sk.k].cpu().numpy().view(np.uint32)
+        else:
+            osk = O.onehash(srp, scl, sk.k, sk.seed)
+            want = O.onehash_values(osk, sk.seed)
+            got = sk.data.view(torch.int32).view(g.n, sk.stride // 4)[rows_t, :sk.k].cpu().numpy().view(np.uint32)
+        row_bad = int(np.count_nonzero(np.any(got != want, axis=1)))
+        cnt = O.pair_counts(srp, scl, est, osk, lu, lv, seed=sk.seed)
+        gc, _, _ = pg.edge_counts(g, sk, est, pairs_d)
+        cnt_bad = int(np.count_nonzero(gc.cpu().numpy() != np.asarray(cnt["count"], np.int32)))
+        e = O.pair_estimates(srp, est, cnt, lu, lv, **kw)
+        T = np.zeros(vs.size)
+        np.add.at(T, np.searchsorted(vs, pu[:nv_pairs]), e[:nv_pairs])
+        T *= 0.5
+        dv = d[vs].astype(np.float64)
+        lcc_want = 2.0 * T / (dv * (dv - 1.0))
+        vs_t = torch.from_numpy(vs).to(g.device)
+        T_got = pipe.out[name]["tri"][vs_t].cpu().numpy()
+        lcc_got = pipe.out[name]["lcc"][vs_t].cpu().numpy().astype(np.float64)
+        t_rel = float(np.max(np.abs(T_got - T) / np.maximum(np.abs(T), 1e-300))) if vs.size else 0.0
+        l_rel = float(np.max(np.abs(lcc_got - lcc_want) / np.maximum(np.abs(lcc_want), 1e-30))) if vs.size else 0.0
+        out[name] = {"rows": int(rows.size), "row_mismatches": row_bad, "pairs": int(pu.size),
+                     "count_mismatches": cnt_bad, "vertices": int(vs.size), "T_max_rel": t_rel,
+                     "lcc_max_rel": l_rel,
+                     "ok": row_bad == 0 and cnt_bad == 0 and t_rel <= 1e-9 and l_rel <= 1e-5}
+    return out
 
 
 # ------------------------------------------------------------ batching
@@ -626,12 +815,18 @@ def run_batch(args, ws, rank, dev):
         tc_exact = torch.zeros(G, dtype=torch.float64, device=dev).index_add_(0, seg, tri) / 3.0
         tc_exact = tc_exact.cpu().numpy()
         est = np.array([r["est_tc"] for r in res])
+        est_l = np.array([r["est_tc_alt"] for r in res])  # the L estimator on the same histograms
         ok = tc_exact > 0
         rel = np.abs(est[ok] - tc_exact[ok]) / tc_exact[ok]
+        rel_l = np.abs(est_l[ok] - tc_exact[ok]) / tc_exact[ok]
         exact = {"ms": ea.elapsed_time(eb), "edges_per_s": m / (ea.elapsed_time(eb) * 1e-3),
                  "tc_rel_error_median": float(np.median(rel)) if rel.size else None,
                  "tc_rel_error_p90": float(np.quantile(rel, 0.9)) if rel.size else None,
-                 "tc_rel_error_total": float((est.sum() - tc_exact.sum()) / tc_exact.sum())}
+                 "tc_rel_error_total": float((est.sum() - tc_exact.sum()) / tc_exact.sum()),
+                 "L_estimator": {
+                     "tc_rel_error_median": float(np.median(rel_l)) if rel_l.size else None,
+                     "tc_rel_error_p90": float(np.quantile(rel_l, 0.9)) if rel_l.size else None,
+                     "tc_rel_error_total": float((est_l.sum() - tc_exact.sum()) / tc_exact.sum())}}
         del gx, wsx
 
     # end to end: the union CSR from pinned host memory, results back to the host
@@ -789,8 +984,7 @@ def run_jp(args, ws, rank, dev):
     achieved = alg / (per["jp_" + dom] * 1e-3) / 1e9
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, e, desc = oracle_sample(rp, cl, dict(w, onehash=None), bits, target_s=15.0)
-        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+        cpu = cpu_baseline(None, rp, cl, dict(w, onehash=None, jaccard=False), bits)
     if rank == 0:
         line = {
             "metric": METRIC + " (Jarvis-Patrick)", "value": m * len(passes) * ws / (ms * 1e-3),
@@ -1089,8 +1283,7 @@ def run_serve(args, ws, rank, dev):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, e, desc = oracle_sample(rp, cl, dict(w, onehash=None), w["bits"], target_s=15.0)
-        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc, "seconds": dt}
+        cpu = cpu_baseline(None, rp, cl, dict(w, onehash=None, jaccard=False), w["bits"])
 
     if rank == 0:
         line = {
@@ -1140,15 +1333,21 @@ def run_reference(args):
         return run_reference_batch(args, ws, dev)
     rp, cl = generate(args.workload, dev)
     bits = cfg.get("bits") or budget_bits(cfg["budget"], rp.numel() - 1, cl.numel())
-    per_step = 4.0 * max(1, 60 // max(args.steps + args.warmup, 1))
+    # every step: a fresh sample run on all host cores (one oracle process per core), about 1.5 s of
+    # work per core, so that K + W steps stay within a few minutes
+    leg = OracleLeg(rp, cl, cfg, bits, seed=1)
+    per_step = 1.5 * leg.cores
     for _ in range(args.warmup):
-        oracle_sample(rp, cl, cfg, bits, target_s=min(per_step, 5.0), seed=1)
-    rates, secs, desc = [], 0.0, ""
+        leg.parallel(leg.sized(per_step, leg.cores))
+    rates, secs, last = [], 0.0, None
     for i in range(args.steps):
-        r, dt, e, desc = oracle_sample(rp, cl, cfg, bits, target_s=per_step, seed=100 + i)
-        rates.append(r)
-        secs += dt
+        chunks = leg.sized(per_step, leg.cores)
+        t0 = time.perf_counter()
+        last = leg.parallel(chunks)
+        secs += time.perf_counter() - t0
+        rates.append(last["value"])
     value = float(np.median(rates))
+    desc = leg.describe(last) if last else ""
     # the same config keys as our arm's line (the generated graphs are simple and symmetric: m = nnz / 2)
     n = int(rp.numel() - 1)
     m = int(cl.numel()) // 2
@@ -1163,8 +1362,9 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f64",
             "data": "synthetic", "config": config,
-            "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "intersections/s", "cores": leg.cores, "kind": "oracle",
+                             "sample": desc,
+                             "formula": "passes * m / (t_build * n / rows + t_pass * m / pairs), median over steps"},
             "e2e": {"value": value, "unit": "intersections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -1208,7 +1408,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--no-parity-sample", action="store_true")
+    ap.add_argument("--source-hash", action="store_true", help="print the pass sources' sha256 and exit")
     args = ap.parse_args()
+    if args.source_hash:
+        print(source_fingerprint())
+        return
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
@@ -1247,6 +1452,27 @@ def main():
     alg = algorithmic_bytes(pipe, dom)
     achieved = alg / (per["pass_" + dom] * 1e-3) / 1e9
     traffic = profiled_traffic(f"{dom}_pass_{args.workload}.md")
+    # every pass against the HBM roofline, and the k-Hash build against the integer ALU roofline
+    clocks = clk.summary()
+    rooflines = {}
+    for nm, sk, _ in pipe.passes:
+        a_nm = algorithmic_bytes(pipe, nm)
+        g_nm = a_nm / (per["pass_" + nm] * 1e-3) / 1e9
+        rooflines["pass_" + nm] = {"bound": "hbm", "achieved": g_nm, "peak": peak, "unit": "GB/s",
+                                   "frac": g_nm / peak, "algorithmic_bytes": a_nm, "ms": per["pass_" + nm],
+                                   "traffic": profiled_traffic(f"{nm}_pass_{args.workload}.md")}
+    for nm, sk, _ in pipe.passes:
+        if sk.kind == pg.SK_KHASH and "build_" + nm in per:
+            mhz = clocks["sm_mhz"] or 2070.0
+            p_alu, sms = alu_peak(mhz)
+            hashes = sk.k * pipe.nnz
+            ops = hashes * ALU_OPS_PER_HASH / (per["build_" + nm] * 1e-3)
+            rooflines["build_" + nm] = {
+                "bound": "alu", "kernel": "k_khash_warp + k_khash_hub", "achieved": ops, "peak": p_alu,
+                "unit": "int32 ALU ops/s", "frac": ops / p_alu, "hashes_per_s": hashes / (per["build_" + nm] * 1e-3),
+                "ms": per["build_" + nm],
+                "peak_derivation": f"{sms} SMs x {ALU_OPS_PER_SM_CLOCK} ALU lane-ops/clock x {mhz:.0f} MHz "
+                                   f"(median sampled SM clock); {ALU_OPS_PER_HASH} ALU ops per hash"}
 
     # end to end from host buffers
     e2e = None
@@ -1283,9 +1509,11 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r, dt, e, desc = oracle_sample(rp, cl, pipe.cfg, pipe.bits, target_s=15.0)
-        cpu = {"value": r, "unit": "intersections/s", "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": dt}
+        cpu = cpu_baseline(pipe, rp, cl, pipe.cfg, pipe.bits)
+
+    parity = None
+    if rank == 0 and not args.no_parity_sample:
+        parity = parity_sample(pipe)
 
     if rank == 0:
         line = {
@@ -1306,11 +1534,13 @@ def main():
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes": alg, "peak_source": peak_kind},
             "e2e": e2e,
+            "rooflines": rooflines,
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "results": res,
             "exact_gpu": exact,
             "cpu_baseline": cpu,
+            "parity_sample": parity,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

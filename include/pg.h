@@ -105,12 +105,16 @@ pg_status pg_validate_csr(const pg_csr *g, int32_t check_symmetry, int64_t *resu
 
 /* ------------------------------------------------------------ edge index */
 /* The upper-edge index: upper_off[u] = number of upper edges (u', v) with
- * u' < u, upper_off[n] = m (undirected edges), and the upper-edge list itself
- * (u, v, d_u and d_v of every edge, in order). It enumerates each edge once for the
- * sum over E of the TC estimator (Sec. VII) and fixes the per-edge output
- * order. Built once per graph and reused by every analysis call. Its size
- * bounds m by nnz / 2 (a symmetric CSR); for a CSR that is not symmetric the
- * list is cut there (pg_validate_csr reports such graphs). */
+ * u' < u, upper_off[n] = m (undirected edges), and the list of upper edges
+ * the passes stream: each edge (u, v) once, grouped by the block of v (blocks
+ * of 2^s vertex ids, s = max(20, ceil(log2 n) - 3), so at most 8 blocks),
+ * each block in upper-edge order, with every entry's upper-edge index (its
+ * per-edge output position). It enumerates each edge once for the sum over E
+ * of the TC estimator (Sec. VII) and fixes the per-edge output order. Built
+ * once per graph and reused by every analysis call; the buffer also holds the
+ * build's scratch. Its size bounds m by nnz / 2 (a symmetric CSR); for a CSR
+ * that is not symmetric the list is cut there (pg_validate_csr reports such
+ * graphs). */
 size_t pg_edge_index_bytes(int32_t n, int64_t nnz);
 /* index: DEVICE buffer of pg_edge_index_bytes(g->n, g->nnz) bytes, 16-byte
  * aligned. Overwritten. Valid for this graph until the graph changes. */
@@ -349,6 +353,33 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
  * stream or synchronise between them. */
 pg_status pg_triangle_count_noalloc(const pg_csr *g, const void *index, const pg_sketch *sk,
                                     int32_t estimator, pg_tc_result *out, pg_stream_t stream);
+
+/* ------------------------------------------- vertex-partitioned runs --
+ * The distributed form of the pass (Sec. VIII-F: the vertices are split
+ * among processes, each builds the sketches of its own vertices, the rows
+ * that its edges need are exchanged, and each estimates the edges of its own
+ * vertices). One rank, holding the whole CSR and index and the exchanged
+ * sketch table, calls pg_partial_sums for its vertex range; the ranks sum
+ * their `sums` and `hist` (element-wise, e.g. an all-reduce; hist as 64-bit
+ * integers, wrapping) and any rank then calls pg_finalize_sums. The results
+ * equal pg_analyze's over the whole graph: the histogram bit for bit, the
+ * per-vertex sums up to the order of double additions.
+ *
+ * pg_partial_sums: the upper edges (u, v) with u_begin <= u < u_end only.
+ * Adds each edge's estimate to sums[u] and sums[v] (DEVICE double [n],
+ * caller-zeroed, or NULL) and its count to hist (DEVICE uint64
+ * [pg_hist_bins], caller-zeroed, or NULL). Workspace as pg_analyze.
+ * PG_ERR_UNSUPPORTED for PG_EST_EXACT and PG_EST_1H_KMV (whose total holds a
+ * 128-bit sum). */
+pg_status pg_partial_sums(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                          int32_t u_begin, int32_t u_end, void *workspace, size_t workspace_bytes,
+                          double *sums, uint64_t *hist, pg_stream_t stream);
+/* pg_finalize_sums: from the summed partials, tc (DEVICE pg_tc_result, from
+ * hist, the fixed-order dot of pg_triangle_count), tri = sums / 2 (DEVICE
+ * double [n], may alias sums) and lcc (DEVICE float [n]); each output is
+ * optional. */
+pg_status pg_finalize_sums(const pg_csr *g, const pg_sketch *sk, int32_t estimator, const uint64_t *hist,
+                           double *sums, pg_tc_result *tc, float *lcc, double *tri, pg_stream_t stream);
 
 /* ----------------------------------------------------- Jarvis-Patrick --
  * Jarvis-Patrick clustering (Sec. III, Listing "Jarvis-Patrick

@@ -38,11 +38,12 @@ EST_BF_OR, EST_BF_SS, EST_1H_KMV = 6, 7, 8
 
 
 def build(force: bool = False) -> str:
-    """Compile pg_oracle.c with the host C compiler (plain -O2, portable)."""
+    """Compile pg_oracle.c with the host C compiler (plain -O3, portable: no
+    machine-specific flags, so the same source builds on x86-64 and Arm)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O3", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -607,6 +607,49 @@ pg_status pg_analyze(const pg_csr *g, const void *index, const pg_sketch *sk, in
     return PG_OK;
 }
 
+// --------------------------------------------------- vertex-partitioned runs
+pg_status pg_partial_sums(const pg_csr *g, const void *index, const pg_sketch *sk, int32_t estimator,
+                          int32_t u_begin, int32_t u_end, void *ws, size_t ws_bytes, double *sums, uint64_t *hist,
+                          pg_stream_t stream) {
+    PG_TRACE("pg_partial_sums");
+    Workspace w;
+    pg_status st = common_checks(g, index, true, sk, estimator, ws, ws_bytes, &w);
+    if (st) return st;
+    PG_REQUIRE(estimator != PG_EST_EXACT && sk != nullptr, PG_ERR_UNSUPPORTED,
+               "pg_partial_sums: the exact count has no partial form here (use pg_analyze)");
+    PG_REQUIRE(estimator != PG_EST_1H_KMV, PG_ERR_UNSUPPORTED,
+               "pg_partial_sums: the KMV total carries a 128-bit sum that does not add word by word");
+    PG_REQUIRE(u_begin >= 0 && u_begin <= u_end && u_end <= g->n, PG_ERR_INVALID_ARG,
+               "pg_partial_sums: vertex range [%d, %d) outside [0, %d]", u_begin, u_end, g->n);
+    PG_REQUIRE((reinterpret_cast<uintptr_t>(sums) & 7u) == 0 && (reinterpret_cast<uintptr_t>(hist) & 7u) == 0,
+               PG_ERR_INVALID_ARG, "pg_partial_sums: misaligned output pointer");
+    if (u_begin == u_end || (!sums && !hist)) return PG_OK;
+    const EdgeIndex ix = edge_index_view(index, g->n, g->nnz);
+    EdgeOutputs eo{};
+    eo.S = sums;
+    eo.hist = hist;
+    eo.u_begin = u_begin;
+    eo.u_end = u_end;
+    PG_TRY_CUDA(launch_intersect_ws(g->row_ptr, g->col, g->n, ix, nullptr, 0, *sk, estimator, eo, w.table, stream),
+                "pg_partial_sums");
+    return PG_OK;
+}
+
+pg_status pg_finalize_sums(const pg_csr *g, const pg_sketch *sk, int32_t estimator, const uint64_t *hist,
+                           double *sums, pg_tc_result *tc, float *lcc, double *tri, pg_stream_t stream) {
+    PG_TRACE("pg_finalize_sums");
+    PG_REQUIRE(g != nullptr && sk != nullptr, PG_ERR_INVALID_ARG, "pg_finalize_sums: graph or sketch is NULL");
+    PG_REQUIRE(g->n >= 0 && (g->n == 0 || g->row_ptr != nullptr), PG_ERR_INVALID_ARG,
+               "pg_finalize_sums: bad graph");
+    PG_REQUIRE(estimator != PG_EST_EXACT && estimator != PG_EST_1H_KMV, PG_ERR_UNSUPPORTED,
+               "pg_finalize_sums: estimator %d has no partial form", estimator);
+    PG_REQUIRE(!tc || hist, PG_ERR_INVALID_ARG, "pg_finalize_sums: tc needs hist");
+    PG_REQUIRE(!(lcc || tri) || sums, PG_ERR_INVALID_ARG, "pg_finalize_sums: lcc / tri need sums");
+    if (tc) PG_TRY_CUDA(launch_tc_finalize(hist, *sk, estimator, tc, stream), "pg_finalize_sums");
+    if (lcc || tri) PG_TRY_CUDA(launch_lcc_finalize(g->row_ptr, g->n, sums, lcc, tri, stream), "pg_finalize_sums");
+    return PG_OK;
+}
+
 // ------------------------------------------------------------ sketch files
 // A sketch file is a 64-byte header followed by the n rows of stride bytes,
 // as they lie in device memory.

@@ -94,17 +94,22 @@ __global__ void __launch_bounds__(kJpThreads) k_jp_init(int32_t *parent, int32_t
     if (blockIdx.x == 0 && threadIdx.x < 2) counters[threadIdx.x] = 0ull;
 }
 
-__global__ void __launch_bounds__(kJpThreads) k_jp_union(EdgeIndex ix, int32_t n, const int32_t *__restrict__ count,
+// count / aux are in the edge list's order (entry e is (eu[e], ev[e])).
+__global__ void __launch_bounds__(kJpThreads) k_jp_union(EdgeIndex ix, int32_t n,
+                                                         const int32_t *__restrict__ count,
                                                          const int32_t *__restrict__ aux, JpTest t, int32_t *parent,
                                                          unsigned long long *kept) {
     int64_t m = ix.upper_off[n];
     if (m > ix.cap) m = ix.cap;
     uint32_t mine = 0;
+    const bool need_deg = t.est != PG_EST_EXACT && t.est != PG_EST_BF_AND && t.est != PG_EST_BF_L;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = __ldg(count + e);
         const int32_t a = aux ? __ldg(aux + e) : 0;
-        if (jp_keep(t, c, a, __ldg(ix.edu + e), __ldg(ix.edv + e))) {
-            jp_unite(parent, __ldg(ix.eu + e), __ldg(ix.ev + e));
+        const int32_t u = __ldg(ix.eu + e), v = __ldg(ix.ev + e);
+        const int32_t ds = need_deg ? __ldg(ix.eds + e) : 0;  // the MinHash tests use d_u + d_v only
+        if (jp_keep(t, c, a, ds, 0)) {
+            jp_unite(parent, u, v);
             ++mine;
         }
     }
@@ -236,6 +241,7 @@ pg_status pg_jarvis_patrick(const pg_csr *g, const void *index, const pg_sketch 
     EdgeOutputs eo{};
     eo.count = count;
     eo.aux = aux;
+    eo.list_order = true;  // k_jp_union walks the list itself
     if (estimator == PG_EST_EXACT) {
         PG_TRY_CUDA(launch_exact_pairs(g->row_ptr, g->col, g->n, ix, nullptr, 0, eo, s), "pg_jarvis_patrick: counts");
     } else {

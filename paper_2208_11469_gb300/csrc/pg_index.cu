@@ -3,9 +3,18 @@
 // The upper-edge index enumerates every undirected edge once, as (u, v) with
 // u < v taken from row u — the sum over E of the TC estimator (Sec. VII)
 // and the per-edge sums of Sec. III. upper_off is the exclusive prefix sum
-// of the per-vertex upper degrees, so edge e belongs to the vertex u with
-// upper_off[u] <= e < upper_off[u+1] and sits at CSR position
-// row_ptr[u+1] - (upper_off[u+1] - e).
+// of the per-vertex upper degrees: upper edge e (the per-edge output order)
+// belongs to the vertex u with upper_off[u] <= e < upper_off[u+1] and sits at
+// CSR position row_ptr[u+1] - (upper_off[u+1] - e).
+//
+// The list the passes stream is the same edges grouped by the block of v:
+// group j holds the edges with v in [j * 2^shift, (j + 1) * 2^shift), each
+// group in upper-edge order (u, then v, ascending), with the degree sum
+// d_u + d_v beside each entry; an entry's upper-edge index follows from the
+// group offsets (upper_pos). A pass that walks the list in order touches,
+// while it is inside one group, only the sketch rows and per-vertex sums of
+// that group's vertices (an L2-sized slice at the largest graphs) besides
+// the row of u, which repeats along the list.
 #include "pg_internal.cuh"
 
 namespace pg {
@@ -28,121 +37,162 @@ __global__ void k_fill_f64(double *p, size_t count, double value) {
         p[i] = value;
 }
 
-// Per-vertex upper degree |{v in N_u : v > u}| by binary search in the
-// sorted row; entry n is set to 0 so that the exclusive scan of n+1
-// entries ends with m.
-__global__ void k_upper_degree(const int32_t *__restrict__ row_ptr,
-                               const int32_t *__restrict__ col, int32_t n,
-                               int32_t *__restrict__ out) {
-    int32_t u = blockIdx.x * blockDim.x + threadIdx.x;
+// Per row u: its upper degree |{v in N_u : v > u}| (binary search for u in the
+// sorted row), and the row's upper part cut by the vertex groups: segment j
+// holds the entries with v >> shift == j. cnt[j * (n + 1) + u] = segment
+// length, seg_end[j * n + u] = CSR position one past the segment. Entry n of
+// upper_off and of every cnt row is set to 0, so that the exclusive scans of
+// n + 1 values end with the totals. Rows of up to 32 upper entries find the
+// cuts by walking them; longer rows by binary search.
+__global__ void k_group_count(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
+                              int32_t shift, int32_t groups, int32_t *__restrict__ upper_off,
+                              int32_t *__restrict__ cnt, int32_t *__restrict__ seg_end) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u > n) return;
     if (u == n) {
-        out[n] = 0;
+        upper_off[n] = 0;
+        for (int32_t j = 0; j < groups; ++j) cnt[(int64_t)j * ((int64_t)n + 1) + n] = 0;
         return;
     }
     int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
     const int32_t end = hi;
     while (lo < hi) {
-        int32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(col + mid) <= u)
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(col + mid) <= (int32_t)u)
             lo = mid + 1;
         else
             hi = mid;
     }
-    out[u] = end - lo;
+    upper_off[u] = end - lo;
+    const bool walk = end - lo <= 32;
+    int32_t cur = lo;
+    for (int32_t j = 0; j < groups; ++j) {
+        int32_t stop = end;
+        if (j + 1 < groups) {
+            const int64_t bound = (int64_t)(j + 1) << shift;
+            if (walk) {
+                stop = cur;
+                while (stop < end && (int64_t)__ldg(col + stop) < bound) ++stop;
+            } else {
+                int32_t a = cur, b = end;
+                while (a < b) {
+                    const int32_t mid = a + ((b - a) >> 1);
+                    if ((int64_t)__ldg(col + mid) < bound)
+                        a = mid + 1;
+                    else
+                        b = mid;
+                }
+                stop = a;
+            }
+        }
+        cnt[(int64_t)j * ((int64_t)n + 1) + u] = stop - cur;
+        seg_end[(int64_t)j * n + u] = stop;
+        cur = stop;
+    }
 }
 
-// The upper-edge list: for upper edge e = (u, v) the index stores eu[e] = u,
-// ev[e] = v and the degrees edu[e] = d_u, edv[e] = d_v, so passes read them as
-// coalesced streams instead of gathering row offsets. The output is cut into
-// chunks of kListChunk edges; a warp takes a chunk, finds the row holding its
-// first edge (a 32-way search over upper_off), and then walks windows of 32
-// consecutive rows: each lane locates the window row of its output position
-// with a binary search over the 32 row ends held in the lanes. Stores are
-// coalesced and each lane has kListUnroll independent loads in flight. Writes
-// at or beyond cap are dropped.
+// The grouped list: entry i = (eu[i], ev[i]) and the degree sum d_u + d_v, eds[i].
+// off = the scanned counts (group j's row u occupies [off_j[u], off_j[u+1]),
+// off_j = off + j * (n + 1)); group j spans [off_j[0], off_j[n]). The output
+// is cut into chunks of kListChunk entries; a warp takes a chunk, finds the
+// group and the row holding its first entry (a 32-way search over off_j), and
+// walks windows of 32 consecutive rows: each lane locates the window row of
+// its output position with a binary search over the 32 segment ends held in
+// the lanes. Stores are coalesced and each lane has kListUnroll independent
+// loads in flight. Writes at or beyond cap are dropped.
 constexpr int32_t kListChunk = 4096;
 constexpr int kListUnroll = 4;
 
-__global__ void __launch_bounds__(256) k_upper_lists(const int32_t *__restrict__ row_ptr,
-                                                     const int32_t *__restrict__ col, int32_t n,
+__global__ void __launch_bounds__(256) k_group_lists(const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col, int32_t n, int32_t groups,
                                                      const int32_t *__restrict__ upper_off,
+                                                     const int32_t *__restrict__ off,
+                                                     const int32_t *__restrict__ seg_end,
                                                      int32_t *__restrict__ eu, int32_t *__restrict__ ev,
-                                                     int32_t *__restrict__ edu, int32_t *__restrict__ edv,
-                                                     int64_t cap) {
+                                                     int32_t *__restrict__ eds, int64_t cap) {
     const unsigned lane = threadIdx.x & 31u;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int64_t m = upper_off[n];
     if (m > cap) m = cap;
     const int64_t chunks = (m + kListChunk - 1) / kListChunk;
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
-        const int64_t c0 = c * kListChunk;
+        int64_t c0 = c * kListChunk;
         const int64_t c1 = c0 + kListChunk < m ? c0 + kListChunk : m;
-        // largest u in [0, n-1] with upper_off[u] <= c0, by a 32-way search
-        int64_t lo = 0, hi = (int64_t)n - 1;
-        while (hi - lo >= 32) {
-            const int64_t step = (hi - lo + 31) / 32;
-            const int64_t probe = lo + (int64_t)lane * step;
-            const bool ok = probe <= hi && upper_off[probe] <= c0;
-            const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            const int last = 31 - __clz((int)bal);  // lane 0 always satisfies ok
-            const int64_t nlo = lo + (int64_t)last * step;
-            hi = (nlo + step - 1 < hi) ? nlo + step - 1 : hi;
-            lo = nlo;
-        }
-        {
-            const int64_t probe = lo + lane;
-            const bool ok = probe <= hi && upper_off[probe] <= c0;
-            const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            lo += 31 - __clz((int)bal);
-        }
-        int64_t u0 = lo;
-        int64_t e = c0;
-        while (e < c1) {
-            // window rows u0 .. u0+31 (lanes past n repeat row n-1)
-            const int64_t ul = u0 + lane < n ? u0 + lane : (int64_t)n - 1;
-            const int32_t off_end = upper_off[ul + 1];
-            const int32_t rp_end = row_ptr[ul + 1];
-            const int32_t deg = rp_end - row_ptr[ul];
-            const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
-            const int64_t wend = c1 < (int64_t)last_end ? c1 : (int64_t)last_end;
-            for (int64_t base = e; base < wend; base += 32 * kListUnroll) {
-                // three phases so that all loads of the kListUnroll edges are in flight together:
-                // locate the row and load v, then gather the degrees of v, then store
-                int32_t vs[kListUnroll], rows[kListUnroll], dus[kListUnroll];
-#pragma unroll
-                for (int j = 0; j < kListUnroll; ++j) {
-                    const int64_t ee = base + 32 * j + lane;
-                    int r = 0;  // window rows whose upper range ends at or before ee
-#pragma unroll
-                    for (int step = 16; step >= 1; step >>= 1) {
-                        const int32_t pr = __shfl_sync(0xffffffffu, off_end, r + step - 1);
-                        if ((int64_t)pr <= ee) r += step;
-                    }
-                    const int rr = r < 31 ? r : 31;
-                    const int32_t oe = __shfl_sync(0xffffffffu, off_end, rr);
-                    const int32_t re = __shfl_sync(0xffffffffu, rp_end, rr);
-                    dus[j] = __shfl_sync(0xffffffffu, deg, rr);
-                    rows[j] = rr;
-                    vs[j] = ee < wend ? __ldg(col + (re - (oe - (int32_t)ee))) : 0;
-                }
-                int32_t dvs[kListUnroll];
-#pragma unroll
-                for (int j = 0; j < kListUnroll; ++j)
-                    dvs[j] = __ldg(row_ptr + vs[j] + 1) - __ldg(row_ptr + vs[j]);
-#pragma unroll
-                for (int j = 0; j < kListUnroll; ++j) {
-                    const int64_t ee = base + 32 * j + lane;
-                    if (ee < wend) {
-                        eu[ee] = (int32_t)(u0 + rows[j]);
-                        ev[ee] = vs[j];
-                        edu[ee] = dus[j];
-                        edv[ee] = dvs[j];
-                    }
-                }
+        while (c0 < c1) {
+            // group of c0: the last j with off_j[0] <= c0 (groups <= 32)
+            const bool gok = (int32_t)lane < groups && (int64_t)off[(int64_t)lane * ((int64_t)n + 1)] <= c0;
+            const int j = 31 - __clz((int)__ballot_sync(0xffffffffu, gok));  // lane 0 always satisfies gok
+            const int32_t *offj = off + (int64_t)j * ((int64_t)n + 1);
+            const int32_t *endj = seg_end + (int64_t)j * n;
+            const int64_t gend = offj[n];
+            const int64_t s1 = c1 < gend ? c1 : gend;
+            // largest u in [0, n-1] with offj[u] <= c0, by a 32-way search
+            int64_t lo = 0, hi = (int64_t)n - 1;
+            while (hi - lo >= 32) {
+                const int64_t step = (hi - lo + 31) / 32;
+                const int64_t probe = lo + (int64_t)lane * step;
+                const bool ok = probe <= hi && offj[probe] <= c0;
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                const int last = 31 - __clz((int)bal);
+                const int64_t nlo = lo + (int64_t)last * step;
+                hi = (nlo + step - 1 < hi) ? nlo + step - 1 : hi;
+                lo = nlo;
             }
-            e = wend > e ? wend : e;
-            u0 += 32;
+            {
+                const int64_t probe = lo + lane;
+                const bool ok = probe <= hi && offj[probe] <= c0;
+                const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                lo += 31 - __clz((int)bal);
+            }
+            int64_t u0 = lo;
+            int64_t e = c0;
+            while (e < s1) {
+                // window rows u0 .. u0+31 (lanes past n repeat row n-1)
+                const int64_t ul = u0 + lane < n ? u0 + lane : (int64_t)n - 1;
+                const int32_t off_end = offj[ul + 1];
+                const int32_t se = endj[ul];
+                const int32_t du = row_ptr[ul + 1] - row_ptr[ul];
+                const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
+                const int64_t wend = s1 < (int64_t)last_end ? s1 : (int64_t)last_end;
+                for (int64_t base = e; base < wend; base += 32 * kListUnroll) {
+                    // three phases so that all loads of the kListUnroll entries are in flight together:
+                    // locate the row and load v, then gather the degrees of v (inside group j's
+                    // vertices, so from L2), then store
+                    int32_t vs[kListUnroll], rows[kListUnroll], dus[kListUnroll];
+#pragma unroll
+                    for (int q = 0; q < kListUnroll; ++q) {
+                        const int64_t ee = base + 32 * q + lane;
+                        int r = 0;  // window rows whose segment ends at or before ee
+#pragma unroll
+                        for (int step = 16; step >= 1; step >>= 1) {
+                            const int32_t pr = __shfl_sync(0xffffffffu, off_end, r + step - 1);
+                            if ((int64_t)pr <= ee) r += step;
+                        }
+                        const int rr = r < 31 ? r : 31;
+                        const int32_t oe = __shfl_sync(0xffffffffu, off_end, rr);
+                        const int32_t sq = __shfl_sync(0xffffffffu, se, rr);
+                        rows[q] = rr;
+                        dus[q] = __shfl_sync(0xffffffffu, du, rr);
+                        vs[q] = ee < wend ? __ldg(col + (sq - (oe - (int32_t)ee))) : 0;
+                    }
+                    int32_t dvs[kListUnroll];
+#pragma unroll
+                    for (int q = 0; q < kListUnroll; ++q)
+                        dvs[q] = __ldg(row_ptr + vs[q] + 1) - __ldg(row_ptr + vs[q]);
+#pragma unroll
+                    for (int q = 0; q < kListUnroll; ++q) {
+                        const int64_t ee = base + 32 * q + lane;
+                        if (ee < wend) {
+                            eu[ee] = (int32_t)(u0 + rows[q]);
+                            ev[ee] = vs[q];
+                            eds[ee] = dus[q] + dvs[q];
+                        }
+                    }
+                }
+                e = wend > e ? wend : e;
+                u0 += 32;
+            }
+            c0 = s1 > c0 ? s1 : c1;
         }
     }
 }
@@ -332,32 +382,66 @@ void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s) {
 
 static int64_t scan_tiles(int64_t count) { return (count + kScanTile - 1) / kScanTile; }
 
-// Index layout: upper_off [n+1] | scan scratch | eu | ev | edu | edv [cap each], where
-// cap = nnz / 2 + 1 bounds m for a symmetric CSR (m = nnz / 2). For a CSR
-// that is not symmetric the lists are cut at cap (consumers read at most cap
-// edges); pg_validate_csr detects such graphs.
+// Index layout: upper_off [n+1] | scan scratch | cnt / offsets [G (n+1)] |
+// segment ends [G n] | eu | ev | eds [cap each], where cap = nnz / 2 + 1
+// bounds m for a symmetric CSR (m = nnz / 2). For a CSR that is not
+// symmetric the lists are cut at cap (consumers read at most cap edges);
+// pg_validate_csr detects such graphs.
 static int64_t list_cap(int64_t nnz) { return nnz / 2 + 1; }
 
-size_t upper_index_bytes(int32_t n, int64_t nnz) {
-    const int64_t count = (int64_t)n + 1;
-    return round_up(sizeof(int32_t) * (size_t)count, 256) +
-           round_up(sizeof(int32_t) * (size_t)scan_tiles(count), 256) +
-           4 * round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
+// Vertex groups of 2^shift ids: at most 8 groups, none below 2^20 vertices
+// (a graph of up to 2^20 vertices is one group).
+int32_t group_shift(int32_t n) {
+    int32_t bits = 0;
+    while (bits < 31 && ((int64_t)1 << bits) < (int64_t)n) ++bits;
+    const int32_t sh = bits - 3;
+    return sh > 20 ? sh : 20;
 }
 
-EdgeIndex edge_index_view(const void *index, int32_t n, int64_t nnz) {
+static int32_t group_count(int32_t n, int32_t shift) {
+    const int64_t g = ((int64_t)n + ((int64_t)1 << shift) - 1) >> shift;
+    return g < 1 ? 1 : (int32_t)g;
+}
+
+namespace {
+struct IndexLayout {
+    size_t scratch, cnt, seg, eu, ev, eds, total;
+};
+IndexLayout index_layout(int32_t n, int64_t nnz) {
     const int64_t count = (int64_t)n + 1;
+    const int32_t G = group_count(n, group_shift(n));
+    IndexLayout L{};
+    size_t o = round_up(sizeof(int32_t) * (size_t)count, 256);
+    L.scratch = o;
+    o += round_up(sizeof(int32_t) * (size_t)scan_tiles((int64_t)G * count), 256);
+    L.cnt = o;
+    o += round_up(sizeof(int32_t) * (size_t)G * (size_t)count, 256);
+    L.seg = o;
+    o += round_up(sizeof(int32_t) * (size_t)G * (size_t)(n > 0 ? n : 1), 256);
+    const size_t lb = round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
+    L.eu = o;
+    L.ev = o + lb;
+    L.eds = o + 2 * lb;
+    L.total = o + 3 * lb;
+    return L;
+}
+}  // namespace
+
+size_t upper_index_bytes(int32_t n, int64_t nnz) { return index_layout(n, nnz).total; }
+
+EdgeIndex edge_index_view(const void *index, int32_t n, int64_t nnz) {
     const uint8_t *b = static_cast<const uint8_t *>(index);
+    const IndexLayout L = index_layout(n, nnz);
     EdgeIndex x;
     x.upper_off = reinterpret_cast<const int32_t *>(b);
-    size_t off = round_up(sizeof(int32_t) * (size_t)count, 256) +
-                 round_up(sizeof(int32_t) * (size_t)scan_tiles(count), 256);
-    x.eu = reinterpret_cast<const int32_t *>(b + off);
-    const size_t lb = round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
-    x.ev = reinterpret_cast<const int32_t *>(b + off + lb);
-    x.edu = reinterpret_cast<const int32_t *>(b + off + 2 * lb);
-    x.edv = reinterpret_cast<const int32_t *>(b + off + 3 * lb);
+    x.eu = reinterpret_cast<const int32_t *>(b + L.eu);
+    x.ev = reinterpret_cast<const int32_t *>(b + L.ev);
+    x.eds = reinterpret_cast<const int32_t *>(b + L.eds);
+    x.goff = reinterpret_cast<const int32_t *>(b + L.cnt);
+    x.seg_end = reinterpret_cast<const int32_t *>(b + L.seg);
     x.cap = list_cap(nnz);
+    x.shift = group_shift(n);
+    x.groups = group_count(n, x.shift);
     return x;
 }
 
@@ -378,21 +462,28 @@ cudaError_t launch_exclusive_scan(int32_t *data, int64_t count, int32_t *scratch
 cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t nnz,
                                void *index, cudaStream_t s) {
     const int64_t count = (int64_t)n + 1;
-    int32_t *upper_off = static_cast<int32_t *>(index);
-    int32_t *scratch = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(index) +
-                                                   round_up(sizeof(int32_t) * (size_t)count, 256));
-    k_upper_degree<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(row_ptr, col, n, upper_off);
+    uint8_t *b = static_cast<uint8_t *>(index);
+    const IndexLayout L = index_layout(n, nnz);
+    const int32_t shift = group_shift(n);
+    const int32_t G = group_count(n, shift);
+    int32_t *upper_off = reinterpret_cast<int32_t *>(b);
+    int32_t *scratch = reinterpret_cast<int32_t *>(b + L.scratch);
+    int32_t *cnt = reinterpret_cast<int32_t *>(b + L.cnt);
+    int32_t *seg = reinterpret_cast<int32_t *>(b + L.seg);
+    k_group_count<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(row_ptr, col, n, shift, G, upper_off, cnt, seg);
     note_launch();
     cudaError_t e = launch_exclusive_scan(upper_off, count, scratch, s);
+    if (e != cudaSuccess) return e;
+    e = launch_exclusive_scan(cnt, (int64_t)G * count, scratch, s);
     if (e != cudaSuccess || n == 0) return e;
-    EdgeIndex x = edge_index_view(index, n, nnz);
     const int64_t chunks = (nnz / 2 + kListChunk) / kListChunk;
     int64_t grid = (chunks + 7) / 8;
     if (grid > 8 * device_info().sm_count) grid = 8 * device_info().sm_count;
     if (grid < 1) grid = 1;
-    k_upper_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, upper_off, const_cast<int32_t *>(x.eu),
-                                                 const_cast<int32_t *>(x.ev), const_cast<int32_t *>(x.edu),
-                                                 const_cast<int32_t *>(x.edv), x.cap);
+    k_group_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, G, upper_off, cnt, seg,
+                                                 reinterpret_cast<int32_t *>(b + L.eu),
+                                                 reinterpret_cast<int32_t *>(b + L.ev),
+                                                 reinterpret_cast<int32_t *>(b + L.eds), list_cap(nnz));
     note_launch();
     return cudaGetLastError();
 }

@@ -106,14 +106,36 @@ __device__ __forceinline__ double fixed_to_f64(unsigned long long x, int frac) {
 void launch_fill_u64(uint64_t *p, size_t count, uint64_t value, cudaStream_t s);
 void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s);
 // View of an upper-edge index buffer (pg_build_edge_index).
+// The upper edges as the passes stream them: grouped by the block of v
+// (2^shift vertex ids per block), each group in upper-edge order.
 struct EdgeIndex {
     const int32_t *upper_off;  // [n+1]
-    const int32_t *eu;         // [cap] u of upper edge e
-    const int32_t *ev;         // [cap] v of upper edge e
-    const int32_t *edu;        // [cap] degree of u
-    const int32_t *edv;        // [cap] degree of v
+    const int32_t *eu;         // [cap] u of list entry i
+    const int32_t *ev;         // [cap] v of list entry i
+    const int32_t *eds;        // [cap] degree sum d_u + d_v of list entry i
+    const int32_t *goff;       // [groups][n+1]: group j's entries of row u are [goff_j[u], goff_j[u+1])
+    const int32_t *seg_end;    // [groups][n]: CSR position one past row u's entries in group j
     int64_t cap;               // list capacity; edges read = min(upper_off[n], cap)
+    int32_t shift;             // vertex group = id >> shift
+    int32_t groups;            // at most kMaxGroups
 };
+constexpr int32_t kMaxGroups = 8;
+// Upper-edge index (per-edge output position) of list entry e = (u, v) of group j.
+__device__ __forceinline__ int64_t upper_pos(const int32_t *row_ptr, int32_t n, const int32_t *upper_off,
+                                             const int32_t *goff, const int32_t *seg_end, int32_t j, int32_t u,
+                                             int64_t e) {
+    const int64_t gs = (int64_t)n + 1;
+    const int64_t pos = (int64_t)__ldg(seg_end + (int64_t)j * n + u) - ((int64_t)__ldg(goff + (int64_t)j * gs + u + 1) - e);
+    return (int64_t)__ldg(upper_off + u + 1) - ((int64_t)__ldg(row_ptr + u + 1) - pos);
+}
+// Group of list entry e (the last j with goff_j[0] <= e).
+__device__ __forceinline__ int32_t list_group(const int32_t *goff, int32_t n, int32_t groups, int64_t e) {
+    int32_t j = 0;
+    for (int32_t t = 1; t < groups; ++t)
+        if ((int64_t)__ldg(goff + (int64_t)t * ((int64_t)n + 1)) <= e) j = t;
+    return j;
+}
+int32_t group_shift(int32_t n);
 size_t upper_index_bytes(int32_t n, int64_t nnz);
 EdgeIndex edge_index_view(const void *index, int32_t n, int64_t nnz);
 size_t scan_scratch_bytes(int64_t count);
@@ -157,6 +179,9 @@ struct EdgeOutputs {
     int32_t *count;     // per edge/pair
     int32_t *aux;       // per edge/pair (1-Hash)
     uint64_t *hist;     // [bins] (zeroed by caller) or null
+    bool list_order;    // per-edge outputs in the edge list's own order (internal), not upper-edge order
+    int32_t u_begin = 0;  // edge source: only the edges (u, v) with u_begin <= u < u_end
+    int32_t u_end = -1;   // -1: every vertex
 };
 // Histogram bins of a pass: Bloom l + 1 (plus one for the OR estimator's
 // degree sum), k-Hash 2 (k + 1), 1-Hash 2 (k + 1)^2 + 2 (k + 1) (plus two for the KMV sum).

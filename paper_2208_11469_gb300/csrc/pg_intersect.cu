@@ -1,9 +1,14 @@
 // Sketch intersection, per-edge estimation and reduction (Sec. IV, Sec. VII).
 //
 // The work is a list of (u, v) pairs: every upper edge of the graph (the
-// lists eu/ev of the edge index, u < v, CSR order) or an explicit pair list.
-// Each warp takes a contiguous range of the list, so the (u, v) loads are
-// coalesced streams and consecutive edges share u.
+// lists eu/ev of the edge index: u < v, grouped by the block of v, each group
+// in CSR order) or an explicit pair list. Edge lists are dealt to the warps in
+// chunks of kChunk consecutive entries, round-robin, so that all warps move
+// through the list together and work inside one group of v at a time (its
+// sketch rows and per-vertex sums stay in L2); a pair list is cut into one
+// contiguous range per warp. Either way the (u, v) loads are coalesced
+// streams and consecutive edges share u. Per-edge outputs go to the edge's
+// upper-edge index, derived from the group offsets of the edge index.
 //   Bloom / k-Hash (k_pass): a group of L lanes holds one sketch row as 16-byte
 //     vectors; per iteration it loads the rows of B edges, counts
 //     popcount(B_u AND B_v) or equal minima lane-wise and reduce-scatters the
@@ -36,8 +41,12 @@ struct Params {
     const int32_t *upper_off;
     const int32_t *eu;      // upper-edge list (edge source)
     const int32_t *ev;
-    const int32_t *edu;     // degrees of u and v per upper edge
-    const int32_t *edv;
+    const int32_t *eds;     // degree sum d_u + d_v of each list entry
+    const int32_t *goff;    // group offsets of the list (groups x (n + 1))
+    const int32_t *seg_end; // per group and row, the CSR position one past the row's entries
+    int32_t groups;
+    int32_t out_upper;      // per-edge outputs at the edge's upper-edge index (else at its list position)
+    int32_t u_begin, u_end; // edge source: only the edges whose u lies in [u_begin, u_end)
     int64_t cap;            // list capacity
     const int32_t *pairs;   // pair list (pair source)
     int64_t P;
@@ -49,6 +58,7 @@ struct Params {
     int32_t est;
     int32_t need_deg;   // per-edge degrees needed
     int32_t need_est;   // per-edge estimate needed (S, cn or jac)
+    int32_t need_out;   // some per-edge output is written (its position is needed)
     const double *table;  // estimator table in global memory
     int32_t table_len;
     // outputs
@@ -135,25 +145,88 @@ __device__ __forceinline__ uint32_t reduce_scatter(uint32_t (&v)[B], unsigned g)
     return v[0];
 }
 
-// Work range of one warp: a contiguous slice of the edge or pair list.
+// The chunks of a warp. A pair list is cut into one contiguous range per
+// warp. An edge list is a sequence of segments, one per vertex group j: the
+// group's entries whose u lies in [u_begin, u_end), which are contiguous
+// (goff_j[u_begin] .. goff_j[u_end]); each segment is padded to whole chunks
+// of kChunk entries in a chunk space, so a chunk never straddles two groups,
+// and the warps take chunks round-robin (warp w: chunks w, w + W, ...). The
+// segment table sits in shared memory, filled by the block's first warp.
+constexpr int64_t kChunk = 1024;
+
+struct SegTable {
+    int64_t beg[kMaxGroups];   // list start of segment j
+    int64_t end[kMaxGroups];   // list end of segment j
+    int64_t vend[kMaxGroups];  // end of segment j in the chunk space
+    int64_t total;             // length of the chunk space
+    int64_t ch;                // chunk size
+    int32_t groups;
+};
+
+// Called by all 32 lanes of one warp.
 template <bool PAIRS>
-__device__ __forceinline__ void warp_range(const Params &p, int64_t &w0, int64_t &w1) {
-    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
-    const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
-    int64_t lo = 0, hi;
+__device__ __forceinline__ void seg_table_fill(const Params &p, SegTable &t, int64_t warps) {
+    const unsigned lane = lane_id();
     if (PAIRS) {
-        hi = p.P;
-    } else {
-        hi = p.upper_off[p.n];
-        if (hi > p.cap) hi = p.cap;
+        if (lane == 0) {
+            t.total = p.P;
+            t.ch = (p.P + warps - 1) / warps;
+            t.groups = 1;
+            t.beg[0] = 0;
+            t.end[0] = p.P;
+            t.vend[0] = p.P;
+        }
+        return;
     }
-    w0 = lo + warp * (hi - lo) / warps;
-    w1 = lo + (warp + 1) * (hi - lo) / warps;
+    int64_t a = 0, b = 0;
+    if ((int32_t)lane < p.groups) {
+        const int32_t *gj = p.goff + (int64_t)lane * ((int64_t)p.n + 1);
+        a = gj[p.u_begin];
+        b = gj[p.u_end];
+        if (b > p.cap) b = p.cap;
+        if (a > b) a = b;
+    }
+    int64_t v = (b - a + kChunk - 1) / kChunk * kChunk;  // inclusive scan of the padded lengths
+#pragma unroll
+    for (int o = 1; o < kMaxGroups; o <<= 1) {
+        const int64_t x = __shfl_up_sync(0xffffffffu, v, o);
+        if ((int)lane >= o) v += x;
+    }
+    if ((int32_t)lane < p.groups) {
+        t.beg[lane] = a;
+        t.end[lane] = b;
+        t.vend[lane] = v;
+    }
+    if ((int32_t)lane == p.groups - 1) {
+        t.total = v;
+        t.ch = kChunk;
+        t.groups = p.groups;
+    }
+}
+
+// List range [w0, w1) of the chunk that starts at vc; returns its group.
+template <bool PAIRS>
+__device__ __forceinline__ int32_t seg_range(const SegTable &t, int64_t vc, int64_t &w0, int64_t &w1) {
+    if (PAIRS) {
+        w0 = vc;
+        w1 = vc + t.ch < t.total ? vc + t.ch : t.total;
+        return 0;
+    }
+    int32_t j = 0;
+    while (j + 1 < t.groups && t.vend[j] <= vc) ++j;
+    const int64_t len = t.end[j] - t.beg[j];
+    const int64_t vstart = t.vend[j] - (len + kChunk - 1) / kChunk * kChunk;
+    w0 = t.beg[j] + (vc - vstart);
+    w1 = w0 + kChunk < t.end[j] ? w0 + kChunk : t.end[j];
+    if (w0 > w1) w0 = w1;
+    return j;
 }
 
 // (u, v) of work item e (u = -1: beyond the range; -2: pair with an id outside
-// [0, n)) and, when want_deg, the two degrees.
-template <bool PAIRS>
+// [0, n)) and, when want_deg, the two degrees. From the edge list with
+// SPLIT = false only their sum is exact (du = d_u + d_v, dv = 0), read from
+// the list itself; with SPLIT, d_u comes from the row offsets.
+template <bool PAIRS, bool SPLIT = true>
 __device__ __forceinline__ void item(const Params &p, int64_t e, int64_t w1, bool want_deg, int32_t &u,
                                      int32_t &v, int32_t &du, int32_t &dv) {
     u = v = -1;
@@ -172,11 +245,20 @@ __device__ __forceinline__ void item(const Params &p, int64_t e, int64_t w1, boo
             u = __ldg(p.eu + e);
             v = __ldg(p.ev + e);
             if (want_deg) {
-                du = __ldg(p.edu + e);
-                dv = __ldg(p.edv + e);
+                const int32_t ds = __ldg(p.eds + e);
+                du = SPLIT ? __ldg(p.row_ptr + u + 1) - __ldg(p.row_ptr + u) : ds;
+                dv = SPLIT ? ds - du : 0;
             }
         }
     }
+}
+
+// Output position of work item e of group j with source u: its upper-edge
+// index for the edge source when per-edge outputs go there, else e itself.
+template <bool PAIRS>
+__device__ __forceinline__ int64_t out_pos(const Params &p, int32_t j, int32_t u, int64_t e) {
+    if (PAIRS || !p.need_out || !p.out_upper || u < 0) return e;
+    return upper_pos(p.row_ptr, p.n, p.upper_off, p.goff, p.seg_end, j, u, e);
 }
 
 // Per-vertex sums at u for the edge source: lanes hold consecutive edges, so
@@ -261,6 +343,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
     }
     if (want_hist)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __shared__ SegTable s_seg;
+    if (threadIdx.x < 32) seg_table_fill<PAIRS>(p, s_seg, (int64_t)gridDim.x * (kThreads >> 5));
     __syncthreads();
 
     const unsigned lane = lane_id();
@@ -269,17 +353,20 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
     const bool owner = (g % S) == 0;
     const int slot = (int)(lane / L) * B + (int)(g / S);  // item offset inside an iteration
 
-    int64_t w0, w1;
-    warp_range<PAIRS>(p, w0, w1);
-    const int32_t iters = (int32_t)((w1 - w0 + E - 1) / E);
-
-    int32_t cu, cv, cdu, cdv;
-    item<PAIRS>(p, w0 + slot, w1, p.need_deg != 0, cu, cv, cdu, cdv);
     int32_t cur_u = -1;  // UREUSE: vertex whose row slice is in cur_row
     unsigned long long dsum = 0ull;  // OR estimator: this lane's sum of d_u + d_v
     uint4 cur_row[VPL];
 #pragma unroll
     for (int q = 0; q < VPL; ++q) cur_row[q] = make_uint4(0u, 0u, 0u, 0u);
+    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
+    for (int64_t vc = warp * s_seg.ch; vc < s_seg.total; vc += warps * s_seg.ch) {
+    int64_t w0, w1;
+    const int32_t gj = seg_range<PAIRS>(s_seg, vc, w0, w1);
+    const int32_t iters = (int32_t)((w1 - w0 + E - 1) / E);
+
+    int32_t cu, cv, cdu, cdv;
+    item<PAIRS>(p, w0 + slot, w1, p.need_deg != 0, cu, cv, cdu, cdv);
     for (int32_t it = 0; it < iters; ++it) {
         const int64_t eb = w0 + (int64_t)it * E;
         // next iteration's work items (independent of this iteration's row loads)
@@ -327,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
         uint32_t c = reduce_scatter<L, B>(part, g);
 
         // ---- epilogue: the owner lane of each edge
-        const int64_t e = eb + slot;
+        const int64_t e = owner ? out_pos<PAIRS>(p, gj, cu, eb + slot) : eb + slot;
         unsigned long long V = 0ull;  // estimate * 2^42
         if (owner && cu == -2) write_zero(p, e);  // invalid pair
         if (owner && cu >= 0) {
@@ -380,6 +467,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
         cdu = ndu;
         cdv = ndv;
     }
+    }
 
     if (want_hist) {
         if (KIND == BLOOM && p.want_union) {
@@ -414,7 +502,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
 // The row of u stays in registers while u repeats (u is non-decreasing along
 // the list); the epilogue is the same as in k_pass, run by every lane for its
 // own item.
-template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
+template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool EDGE_OUT>
 __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     // W: 32-bit words of the row payload (l / 32 for Bloom, k for k-Hash)
     constexpr int NV = (W + 3) / 4;  // vectors per row
@@ -439,6 +527,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     }
     if (want_hist)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __shared__ SegTable s_seg;
+    if (threadIdx.x < 32) seg_table_fill<false>(p, s_seg, (int64_t)gridDim.x * (kThreads >> 5));
     __syncthreads();
 
     const unsigned lane = lane_id();
@@ -453,19 +543,22 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const bool need_deg = p.need_deg != 0;
     const uint8_t *rowbase = p.data + 16 * vidx;
 
+    int32_t cur_u = -1;
+    uint4 cur_row = make_uint4(0u, 0u, 0u, 0u);
+    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
+    for (int64_t vc = warp * s_seg.ch; vc < s_seg.total; vc += warps * s_seg.ch) {
     int64_t w0, w1;
-    warp_range<false>(p, w0, w1);
+    const int32_t gj = seg_range<false>(s_seg, vc, w0, w1);
     const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
 
     int32_t cu, cv, cdu, cdv;
-    item<false>(p, w0 + lane, w1, need_deg, cu, cv, cdu, cdv);
-    int32_t cur_u = -1;
-    uint4 cur_row = make_uint4(0u, 0u, 0u, 0u);
+    item<false, EDGE_OUT>(p, w0 + lane, w1, need_deg, cu, cv, cdu, cdv);
 
     for (int32_t it = 0; it < iters; ++it) {
         const int64_t eb = w0 + (int64_t)it * 32;
         int32_t nu, nv, ndu, ndv;
-        item<false>(p, eb + 32 + lane, w1, need_deg, nu, nv, ndu, ndv);
+        item<false, EDGE_OUT>(p, eb + 32 + lane, w1, need_deg, nu, nv, ndu, ndv);
         uint32_t c = 0;
 #pragma unroll
         for (int s0 = 0; s0 < L; s0 += SB) {
@@ -510,10 +603,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
         }
 
         // ---- epilogue: every lane, for its own item
-        const int64_t e = eb + lane;
+        const int64_t e = EDGE_OUT ? out_pos<false>(p, gj, cu, eb + lane) : eb + lane;
         unsigned long long V = 0ull;
         if (cu >= 0) {
-            if (KIND == KHASH && (cdu == 0 || cdv == 0)) c = 0;
+            // (edges of the list join two vertices of degree >= 1: no empty sketch here)
             float est_f = 0.0f;
             double est_d = 0.0;
             if (KIND == BLOOM) {
@@ -538,8 +631,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
                     if (old + ds < old) atomicAdd(h32 + 2 * hk + c, 1u);
                 }
             }
-            if (p.count) p.count[e] = (int32_t)c;
-            write_sims(p, e, est_f, cdu, cdv);
+            if (EDGE_OUT) {
+                if (p.count) p.count[e] = (int32_t)c;
+                write_sims(p, e, est_f, cdu, cdv);
+            }
             if (p.S) atomicAdd(p.S + cv, est_d);
         }
         if (p.S) add_u_runs(p.S, cu, V);
@@ -547,6 +642,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
         cv = nv;
         cdu = ndu;
         cdv = ndv;
+    }
     }
 
     if (want_hist) {
@@ -633,20 +729,26 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
     }
     if (want_hist)
         for (int i = threadIdx.x; i < h32_len; i += blockDim.x) h32[i] = 0u;
+    __shared__ SegTable s_seg;
+    if (threadIdx.x < 32) seg_table_fill<PAIRS>(p, s_seg, (int64_t)gridDim.x * (kThreads >> 5));
     __syncthreads();
 
     const int nv4 = (int)((k + 3) / 4);
-    int64_t w0, w1;
-    warp_range<PAIRS>(p, w0, w1);
-    const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
     const bool kmv = p.est == PG_EST_1H_KMV;
     // KMV totals: this lane's sum of the real union estimates (k - 1) 2^32 / (h_k + 1) of its
     // edges whose union sketch is full, as an exact 128-bit integer x 2^-52
     unsigned long long rlo = 0ull, rhi = 0ull;
+    const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
+    for (int64_t vc = warp * s_seg.ch; vc < s_seg.total; vc += warps * s_seg.ch) {
+    int64_t w0, w1;
+    const int32_t gj = seg_range<PAIRS>(s_seg, vc, w0, w1);
+    const int32_t iters = (int32_t)((w1 - w0 + 31) / 32);
     for (int32_t it = 0; it < iters; ++it) {
-        const int64_t e = w0 + (int64_t)it * 32 + lane;
+        const int64_t ei = w0 + (int64_t)it * 32 + lane;
         int32_t cu, cv, cdu, cdv;
-        item<PAIRS>(p, e, w1, true, cu, cv, cdu, cdv);
+        item<PAIRS>(p, ei, w1, true, cu, cv, cdu, cdv);
+        const int64_t e = out_pos<PAIRS>(p, gj, cu, ei);
         const bool valid = cu >= 0;
         const uint32_t la = valid ? min(k, (uint32_t)cdu) : 0u, lb = valid ? min(k, (uint32_t)cdv) : 0u;
         // stage the two rows (whole 16-byte vectors; entries past min(k, d) are never read)
@@ -746,6 +848,7 @@ __global__ void __launch_bounds__(kThreads) k_onehash(Params p) {
                 if (old + ldsum < old) atomicAdd(h32 + 3 * hk2 + 2 * hk + lbin, 1u);
             }
         }
+    }
     }
 
     if (want_hist && kmv) {
@@ -973,7 +1076,8 @@ template <int KIND, int L, int W, int SB, bool UREUSE, int MINB>
 cudaError_t run_lean(const Params &p, cudaStream_t s) {
     const int h32_len = (KIND == BLOOM) ? (int)p.l + 1 : 3 * ((int)p.k + 1);
     const size_t smem = 20 * (size_t)round_up4(p.table_len) + (p.hist ? 4 * (size_t)h32_len : 0);
-    auto kern = k_lean<KIND, L, W, SB, UREUSE, MINB>;
+    // per-edge outputs take their own instance, so that passes without them carry none of that code
+    auto kern = p.need_out ? k_lean<KIND, L, W, SB, UREUSE, MINB, true> : k_lean<KIND, L, W, SB, UREUSE, MINB, false>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1026,8 +1130,13 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     p.upper_off = ix.upper_off;
     p.eu = ix.eu;
     p.ev = ix.ev;
-    p.edu = ix.edu;
-    p.edv = ix.edv;
+    p.eds = ix.eds;
+    p.out_upper = out.list_order ? 0 : 1;
+    p.goff = ix.goff;
+    p.seg_end = ix.seg_end;
+    p.groups = ix.groups;
+    p.u_begin = out.u_begin;
+    p.u_end = out.u_end < 0 ? n : out.u_end;
     p.cap = ix.cap;
     p.pairs = pairs;
     p.P = P;
@@ -1050,6 +1159,7 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     p.table_len = (int32_t)table_len(sk.kind, sk.bits, sk.k);
     const bool sims = out.jac || out.ovl || out.tot;
     p.need_est = (out.S || out.cn || sims) ? 1 : 0;
+    p.need_out = (out.count || out.aux || out.cn || sims) ? 1 : 0;
     p.need_deg = (sk.kind != PG_SK_BLOOM || sims || p.want_union) ? 1 : 0;
     k_table<<<1, 256, 0, s>>>(table_ws, p.table_len, sk.kind, estimator, sk.bits, sk.b, sk.k);
     note_launch();

@@ -14,7 +14,9 @@
 //   - The array is kNoallocScratchBytes (64 KiB) of static device memory. Every
 //     GPU that loads the library holds it until the process exits.
 //   - It covers every sketch configuration the library supports (largest:
-//     1-Hash with k = 32, about 27 KiB); the exact estimator needs scratch
+//     1-Hash with k = 32 read by the KMV estimator, 22,016 table bytes plus
+//     2,246 histogram words = 39,984 bytes, about 39 KiB; Bloom with l = 1024
+//     and the OR estimator needs about 28 KiB); the exact estimator needs scratch
 //     proportional to the graph and is rejected with PG_ERR_UNSUPPORTED.
 //   - The first call on each device looks up the array's device address
 //     (with that device current). Make that first call before any stream

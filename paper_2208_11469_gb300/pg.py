@@ -35,6 +35,7 @@ SYMBOLS = [
     "pg_upload_build", "pg_sketch_save", "pg_sketch_load_header", "pg_sketch_load",
     "pg_hist_bins", "pg_workspace_bytes", "pg_triangle_count", "pg_clustering",
     "pg_jaccard_pairs", "pg_similarity_pairs", "pg_edge_counts", "pg_kernel_launches", "pg_analyze", "pg_triangle_count_noalloc",
+    "pg_partial_sums", "pg_finalize_sums",
     "pg_jarvis_patrick_workspace_bytes", "pg_jarvis_patrick", "pg_clique4_workspace_bytes", "pg_clique4_count",
     "pg_batch_autotune", "pg_batch_workspace_bytes", "pg_batch_create", "pg_batch_run", "pg_batch_run_host",
     "pg_batch_destroy",
@@ -166,6 +167,8 @@ def lib() -> ctypes.CDLL:
                 "pg_kernel_launches": (ctypes.c_uint64, []),
                 "pg_analyze": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, sz, P(Outputs), vp]),
                 "pg_triangle_count_noalloc": (i32, [P(Csr), vp, P(SketchDesc), i32, vp, vp]),
+                "pg_partial_sums": (i32, [P(Csr), vp, P(SketchDesc), i32, i32, i32, vp, sz, vp, vp, vp]),
+                "pg_finalize_sums": (i32, [P(Csr), P(SketchDesc), i32, vp, vp, vp, vp, vp, vp]),
                 "pg_jarvis_patrick_workspace_bytes": (sz, [P(Csr), P(SketchDesc), i32]),
                 "pg_clique4_workspace_bytes": (sz, [P(Csr), i32, u32]),
                 "pg_clique4_count": (i32, [P(Csr), i32, u32, u32, u32, vp, sz, vp, vp]),
@@ -543,6 +546,38 @@ def triangle_count_noalloc(g: Graph, sk: Sketch, est: int, *, out: torch.Tensor 
     _check(lib().pg_triangle_count_noalloc(ctypes.byref(c), _ptr(g.index), dref, est, _ptr(out), _stream()),
            "pg_triangle_count_noalloc")
     return read_tc_result(out) if read else out
+
+
+# -------------------------------------------------- vertex-partitioned runs
+def partial_sums(g: Graph, sk: Sketch, est: int, u_begin: int, u_end: int, *, sums: torch.Tensor | None = None,
+                 hist: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """pg_partial_sums: the estimates of the upper edges (u, v) with
+    u_begin <= u < u_end added into sums (double [n]) at both endpoints and
+    their counts into hist (int64 [hist_bins]); both are zeroed here when
+    not given."""
+    ws = ws if ws is not None else workspace(g, sk, est)
+    if sums is None:
+        sums = torch.zeros(g.n, dtype=torch.float64, device=g.device)
+    if hist is None:
+        hist = torch.zeros(max(hist_bins(sk, est), 1), dtype=torch.int64, device=g.device)
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_partial_sums(ctypes.byref(c), _ptr(g.index), dref, est, int(u_begin), int(u_end), _ptr(ws),
+                                 ws.numel(), _ptr(sums), _ptr(hist), _stream()), "pg_partial_sums")
+    return sums, hist
+
+
+def finalize_sums(g: Graph, sk: Sketch, est: int, hist: torch.Tensor, sums: torch.Tensor, *,
+                  tc: torch.Tensor | None = None, lcc: torch.Tensor | None = None, tri: torch.Tensor | None = None):
+    """pg_finalize_sums: TC from a summed histogram, T = sums / 2 and LCC."""
+    tc = tc if tc is not None else tc_result_buffer(g.device)
+    lcc = lcc if lcc is not None else torch.empty(g.n, dtype=torch.float32, device=g.device)
+    tri = tri if tri is not None else torch.empty(g.n, dtype=torch.float64, device=g.device)
+    c = g.csr()
+    d, dref = _sk_args(sk)
+    _check(lib().pg_finalize_sums(ctypes.byref(c), dref, est, _ptr(hist), _ptr(sums), _ptr(tc), _ptr(lcc), _ptr(tri),
+                                  _stream()), "pg_finalize_sums")
+    return tc, lcc, tri
 
 
 # ------------------------------------------------------------ Jarvis-Patrick

@@ -253,22 +253,34 @@ def test_64_bit_build_with_hub_rows(pg):
 @pytest.mark.gpu
 def test_batch_against_oracle(pg):
     from oracle import oracle as O
-    parts = synth.batch_mix(4, seed=3, log2_n=(7, 10))
-    cfg = [(256, 2), (256, 2), (512, 1), (128, 4)]
+    # every bucket width, the 64-bit one (flat-walk build and pull pass) included, and a
+    # 64-bit graph with a 9 500-neighbour hub row
+    parts = synth.batch_mix(9, seed=3, log2_n=(7, 10))
+    n_h = 12000
+    rp_h, cl_h = synth.erdos_renyi(n_h, 6.0, seed=4)
+    src = torch.repeat_interleave(torch.arange(n_h), (rp_h[1:] - rp_h[:-1]).long())
+    hub = torch.randperm(n_h, generator=torch.Generator().manual_seed(2))[:9500]
+    hub_graph = synth.csr_from_pairs(torch.cat([src, torch.full((9500,), 77, dtype=torch.int64)]),
+                                     torch.cat([cl_h.long(), hub]), n_h)
+    parts = parts[:6] + [hub_graph] + parts[6:]
+    # graphs of one (bits, b) bucket are contiguous
+    cfg = [(256, 2), (256, 2), (512, 1), (128, 4), (64, 1), (64, 2), (64, 2), (64, 4), (1024, 2), (128, 1)]
     rp, cl, voff = synth.block_diagonal(parts)
-    batch = pg.Batch(pg.graph(rp.cuda(), cl.cuda(), build_index=False), voff, cfg, seed=9)
+    batch = pg.Batch(pg.graph(rp.cuda(), cl.cuda(), build_index=False), voff, cfg, seed=9, want_tri=True)
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         batch.run()
     side.synchronize()
     got = batch.results()
     lcc = batch.lcc.cpu().numpy()
+    tri = batch.tri.cpu().numpy()
     for i, ((prp, pcl), (bits, b)) in enumerate(zip(parts, cfg)):
         ref = O.analyze(prp.numpy(), pcl.numpy(), O.EST_BF_AND, l=bits, b=b, seed=9)
-        assert got[i]["edges"] == ref["m"]
-        assert got[i]["count_sum"] == int(np.sum(ref["counts"]["count"]))
-        assert got[i]["est_tc"] == pytest.approx(ref["tc"], rel=RTOL_F64)
+        assert got[i]["edges"] == ref["m"], i
+        assert got[i]["count_sum"] == int(np.sum(ref["counts"]["count"])), i
+        assert got[i]["est_tc"] == pytest.approx(ref["tc"], rel=RTOL_F64), i
         np.testing.assert_allclose(lcc[voff[i]:voff[i + 1]], ref["lcc"], rtol=RTOL_F32, atol=1e-6)
+        np.testing.assert_allclose(tri[voff[i]:voff[i + 1]], ref["T"], rtol=RTOL_F64, atol=1e-9)
     batch.close()
 
 

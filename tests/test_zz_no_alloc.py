@@ -36,6 +36,9 @@ def pg():
     ("er", "khash", dict(k=256), 3),
     ("rmat", "onehash", dict(k=32), 4),
     ("rmat", "onehash", dict(k=32), 5),
+    ("rmat", "onehash", dict(k=32), 8),   # KMV: the largest scratch (two extra histogram words)
+    ("rmat", "bloom", dict(bits=1024, b=2), 6),  # OR: one extra histogram bin
+    ("er", "bloom", dict(bits=448, b=2), 7),     # single-set estimator
 ])
 def test_noalloc_matches_workspace_entry_point_twice(pg, graph, kind, params, est):
     rp, cl = synth.erdos_renyi(4096, 16.0, seed=1) if graph == "er" else synth.rmat(13, 16, seed=3)
