@@ -540,7 +540,7 @@ class OracleLeg:
             rows = np.sort(self.order[self.next_row:self.next_row + r])
             self.next_row += r
             rp, cl = host_sub_csr(self.rp, self.col_d, rows)
-            out.append(dict(rp=rp, cl=cl, pairs=max(1, E // parts), table_rows=table_rows,
+            out.append(dict(rp=rp, cl=cl, rows=rows, pairs=max(1, E // parts), table_rows=table_rows,
                             pair_seed=int(self.rng.integers(1 << 31))))
         return out
 

@@ -108,7 +108,7 @@ __device__ __forceinline__ uint32_t lane_intersect(const int32_t *A, int32_t la,
 
 constexpr int kWarpList = 256;   // oriented list length handled by one warp
 constexpr int kBlockThreads = 512;
-constexpr int kBlockListBytes = 128 * 1024;  // shared-memory hash table of the block kernel
+constexpr int kBlockListBytes = 32 * 1024;  // shared-memory hash table of the block kernel (4 blocks per SM)
 
 constexpr int kHashSlots = 2 * kWarpList;  // open-addressing table of N+_u, at most half full
 
@@ -392,11 +392,11 @@ cudaError_t launch_exact_tc(const int32_t *row_ptr, const int32_t *col, int32_t 
         k_exact_long_list<<<persistent_grid(), kThreads, 0, s>>>(plus_off, n, long_count, long_ids);
         if (S) {
             k_exact_warp<true><<<persistent_grid(), kThreads, 0, s>>>(plus_off, plus_col, n, S, counter);
-            k_exact_block<true><<<2 * device_info().sm_count, kBlockThreads, kBlockListBytes, s>>>(
+            k_exact_block<true><<<4 * device_info().sm_count, kBlockThreads, kBlockListBytes, s>>>(
                 plus_off, plus_col, long_count, long_ids, S, counter);
         } else {
             k_exact_warp<false><<<persistent_grid(), kThreads, 0, s>>>(plus_off, plus_col, n, S, counter);
-            k_exact_block<false><<<2 * device_info().sm_count, kBlockThreads, kBlockListBytes, s>>>(
+            k_exact_block<false><<<4 * device_info().sm_count, kBlockThreads, kBlockListBytes, s>>>(
                 plus_off, plus_col, long_count, long_ids, S, counter);
         }
         note_launch(5);

@@ -248,6 +248,19 @@ __device__ __forceinline__ void khash_slice(const int32_t *__restrict__ col, int
     for (int32_t base = a; base < e; base += 32) {
         const int32_t cnt = min(32, e - base);
         const uint32_t px_mine = (lane < (unsigned)cnt) ? fmix_pre((uint32_t)__ldg(col + base + lane)) : 0u;
+        if (P == 1 && cnt == 32) {
+            // a full chunk, two entries per step: one three-input min takes both hashes, and no
+            // per-entry bound check
+#pragma unroll 4
+            for (int s = 0; s < 32; s += 2) {
+                const uint32_t p1 = __shfl_sync(0xffffffffu, px_mine, s);
+                const uint32_t p2 = __shfl_sync(0xffffffffu, px_mine, s + 1);
+#pragma unroll
+                for (int t = 0; t < KPL; ++t)
+                    mn[t] = __vimin3_u32(mn[t], hash_pre(p1, pre_s[t]), hash_pre(p2, pre_s[t]));
+            }
+            continue;
+        }
         for (int s = 0; s < cnt; s += P) {
             const int src = s + (int)part;
             const uint32_t px = __shfl_sync(0xffffffffu, px_mine, src & 31);

@@ -55,3 +55,33 @@ def test_thm71_radius():
     assert 2 * m * m * C / (9 * tb * tb) == pytest.approx(delta, rel=1e-12)
     assert out["bf_small"]["t"] is None and "0.499" in out["bf_small"]["reason"]  # 16 * max d > 0.499 * 64 ln 64
     assert out["x"] is None
+
+
+def test_oracle_leg_samples_the_whole_graph():
+    """The CPU leg's sample: uniformly drawn rows without repeats within a run
+    of chunks, sub-CSRs that hold each sampled row's own neighbours (so their
+    sketches are the whole graph's), pass tables no smaller than the rows, and
+    a whole-graph time that scales the sample's phases by n/R and m/E."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import sample_timing as ST
+    from paper_2208_11469_gb300 import synth
+    rp, cl = synth.rmat(12, 8, seed=2)
+    leg = bench.OracleLeg(rp, cl, dict(bench.WORKLOADS["er4096"]), 256, seed=3)
+    chunks = leg.chunks(1200, 4000, 4)
+    assert len(chunks) == 4 and all(c["pairs"] == 1000 for c in chunks)
+    rpn, cln = rp.numpy(), cl.numpy()
+    all_rows = np.concatenate([c["rows"] for c in chunks])
+    assert all_rows.size == 1200 and np.unique(all_rows).size == 1200
+    for c in chunks:
+        d = np.diff(c["rp"])
+        assert c["rp"][0] == 0 and d.sum() == c["cl"].size and c["table_rows"] >= d.size
+        for i, v in enumerate(c["rows"]):
+            assert np.array_equal(c["cl"][c["rp"][i]:c["rp"][i + 1]], cln[rpn[v]:rpn[v + 1]])
+    r = ST.time_chunk(chunks[0]["rp"], chunks[0]["cl"], leg.passes, 500, 2000, pair_seed=1)
+    assert r["pairs"] == 500 and r["table_rows"] == 2000 and r["rows"] == chunks[0]["rp"].size - 1
+    assert set(r["t_pass"]) == {"bloom", "khash"} and r["build_s"] > 0 and r["pass_s"] > 0
+    rate, T = leg._rate(2.0, 1.0, 100, 1000)
+    assert T == pytest.approx(2.0 * leg.n / 100 + 1.0 * leg.m / 1000)
+    assert rate == pytest.approx(2 * leg.m / T)
