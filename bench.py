@@ -360,20 +360,44 @@ def time_steps(pipe: Pipeline, steps: int, warmup: int, ws: int):
     names = pipe.event_names()
     evs = [{nm: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for nm in names}
            for _ in range(steps)]
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     launches0 = pipe.pg.kernel_launches()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(ws)
     torch.cuda.synchronize()
-    start.record()
+    marks[0].record()
     for i in range(steps):
         pipe.step(evs[i])
-    end.record()
+        marks[i + 1].record()
     torch.cuda.synchronize()
     barrier(ws)
     launches = pipe.pg.kernel_launches() - launches0
-    total_ms = start.elapsed_time(end)
+    total_ms = marks[0].elapsed_time(marks[-1])
     per = {nm: float(np.mean([e[nm][0].elapsed_time(e[nm][1]) for e in evs])) for nm in names}
-    return total_ms / steps, per, launches
+    step_ms = [marks[i].elapsed_time(marks[i + 1]) for i in range(steps)]
+    return total_ms / steps, per, launches, step_stats(step_ms)
+
+
+def step_stats(ms):
+    """Median of the per-step times and its 95% non-parametric confidence
+    interval (order statistics of a Binomial(K, 1/2) around the median; the
+    whole range below 6 steps)."""
+    x = np.sort(np.asarray(ms, dtype=np.float64))
+    k = x.size
+    if k == 0:
+        return None
+    lo, hi = 0, k - 1
+    if k >= 6:
+        from math import comb
+        # the median lies below x_(lo) (0-based) with probability P(Bin(k, 1/2) <= lo): take the
+        # largest lo with that at most 2.5%, and the mirror image above
+        cdf, j = 0.0, 0
+        while True:
+            nxt = cdf + comb(k, j) / 2.0**k
+            if nxt > 0.025:
+                break
+            cdf, j = nxt, j + 1
+        lo, hi = j - 1, k - j
+    return {"median": float(np.median(x)), "ci95": [float(x[lo]), float(x[hi])], "steps": int(k)}
 
 
 def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
@@ -1440,7 +1464,7 @@ def main():
     torch.cuda.synchronize()
 
     with ClockSampler(local) as clk:
-        ms, per, launches = time_steps(pipe, args.steps, args.warmup, ws)
+        ms, per, launches, stats = time_steps(pipe, args.steps, args.warmup, ws)
     ms_max = max_over_ranks(ms, ws, dev)
     units = pipe.sketched_per_step() * ws
     value = units / (ms_max * 1e-3)
@@ -1528,6 +1552,7 @@ def main():
                        "l2": "inputs larger than L2 (CSR and sketch tables >> 129 MB), no flush",
                        "parallelism": f"replicas x{ws}"},
             "phases_ms": per,
+            "step_ms": stats,
             "roofline": {"bound": "hbm",
                          "kernel": ("k_onehash" if dict((p[0], p[1]) for p in pipe.passes)[dom].kind == pg.SK_1HASH
                                     else "k_lean") + f" ({dom} pass of pg_analyze)", "achieved": achieved,

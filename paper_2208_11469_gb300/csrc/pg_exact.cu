@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kThreads) k_exact_pairs(const int32_t *__restr
         for (int o = kL / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (e < e1 && g == 0) {
             // outputs: pairs and list-order requests at e, upper edges at their upper-edge index
-            const int64_t o = (PAIRS || list_order)
+            const int64_t o = (PAIRS || list_order || ix.groups == 1)
                                   ? e
                                   : upper_pos(row_ptr, n, ix.upper_off, ix.goff, ix.seg_end,
                                               list_group(ix.goff, n, ix.groups, e), xu, e);

@@ -257,7 +257,8 @@ __device__ __forceinline__ void item(const Params &p, int64_t e, int64_t w1, boo
 // index for the edge source when per-edge outputs go there, else e itself.
 template <bool PAIRS>
 __device__ __forceinline__ int64_t out_pos(const Params &p, int32_t j, int32_t u, int64_t e) {
-    if (PAIRS || !p.need_out || !p.out_upper || u < 0) return e;
+    // one group: the list is in upper-edge order itself
+    if (PAIRS || !p.need_out || !p.out_upper || u < 0 || p.groups == 1) return e;
     return upper_pos(p.row_ptr, p.n, p.upper_off, p.goff, p.seg_end, j, u, e);
 }
 
