@@ -281,6 +281,7 @@ class Pipeline:
                 o["edge_total"] = torch.empty(self.m, dtype=torch.float32, device=dev)
             self.out[name] = o
         self.index_events = None
+        self.side = torch.cuda.Stream(device=dev)
 
     def sketched_per_step(self) -> int:
         return self.m * len(self.passes)
@@ -296,17 +297,25 @@ class Pipeline:
 
     def step(self, ev=None, builds=True):
         """One pass of the hot path. ev: optional dict name -> (start, end) events.
-        builds=False: the sketches are already built (by upload_build)."""
+        builds=False: the sketches are already built (by upload_build).
+
+        The edge index depends only on the CSR and the sketch builds only on the
+        CSR, so the index runs on a side stream beside the builds (it is bound by
+        memory latency, the builds largely by issue); the passes wait for both."""
         pg, g = self.pg, self.g
         s = torch.cuda.current_stream()
+        side = self.side if builds else s
 
-        def mark(name, i):
+        def mark(name, i, stream=None):
             if ev is not None:
-                ev[name][i].record(s)
+                ev[name][i].record(stream or s)
 
-        mark("index", 0)
-        pg.build_edge_index_into(g)
-        mark("index", 1)
+        if side is not s:
+            side.wait_stream(s)
+        with torch.cuda.stream(side):
+            mark("index", 0, side)
+            pg.build_edge_index_into(g)
+            mark("index", 1, side)
         built = set() if builds else {id(sk) for _, sk, _ in self.passes}
         for name, sk, est in self.passes:
             if id(sk) in built:
@@ -318,6 +327,8 @@ class Pipeline:
             else:
                 pg.build_minhash(g, sk.kind, sk.k, sk.seed, out=sk, workspace=self.build_ws)
             mark("build_" + name, 1)
+        if side is not s:
+            s.wait_stream(side)
         for name, sk, est in self.passes:
             mark("pass_" + name, 0)
             pg.analyze(g, sk, est, ws=self.ws[name], **self.out[name])
