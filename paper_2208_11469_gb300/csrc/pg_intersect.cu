@@ -506,9 +506,12 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pass(Params p) {
 template <int KIND, int L, int W, int SB, bool UREUSE, int MINB, bool EDGE_OUT>
 __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     // W: 32-bit words of the row payload (l / 32 for Bloom, k for k-Hash)
-    constexpr int NV = (W + 3) / 4;  // vectors per row
-    static_assert(NV <= L, "a row must fit one vector per lane");
-    constexpr bool kRedux = (KIND == KHASH && L == 16);
+    constexpr int NV = (W + 3) / 4;               // vectors per row
+    constexpr int VPL = (NV + L - 1) / L;          // vectors per lane: vector g + q L for q < VPL
+    static_assert(VPL <= 2, "a row must fit two vectors per lane");
+    // k-Hash match counts (at most 64 for the packed forms) of all groups in one integer
+    // reduction: 2 groups x 16 bits (L = 16) or 4 groups x 8 bits (L = 8)
+    constexpr int kPack = (KIND == KHASH && L == 16) ? 16 : (KIND == KHASH && L == 8 && W <= 255) ? 8 : 0;
     extern __shared__ __align__(16) unsigned char smem[];
     double *tab = reinterpret_cast<double *>(smem);
     unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
@@ -535,17 +538,24 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     const unsigned lane = lane_id();
     const unsigned g = lane & (L - 1);
     const int grp = (int)(lane / L);
-    // Lanes past the row's vectors read vector 0 (inside the row) and count nothing.
-    const int vidx = (int)g < NV ? (int)g : 0;
-    // Word j of this lane's vector is payload iff 4g + j < W (compile-time for full rows).
-    const bool ok0 = (int)(4 * g + 0) < W, ok1 = (int)(4 * g + 1) < W;
-    const bool ok2 = (int)(4 * g + 2) < W, ok3 = (int)(4 * g + 3) < W;
-    const uint32_t grp_shift = (uint32_t)grp * 16u;
+    // Lanes past the row's vectors read vector 0 (inside the row) and count nothing;
+    // word j of vector x is payload iff 4x + j < W (compile-time for full rows).
+    bool ok[VPL][4];
+    const uint8_t *rowbase[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) {
+        const int x = (int)g + q * L;
+        rowbase[q] = p.data + 16 * (x < NV ? x : 0);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) ok[q][w] = 4 * x + w < W;
+    }
+    const uint32_t grp_shift = (uint32_t)grp * (uint32_t)kPack;
     const bool need_deg = p.need_deg != 0;
-    const uint8_t *rowbase = p.data + 16 * vidx;
 
     int32_t cur_u = -1;
-    uint4 cur_row = make_uint4(0u, 0u, 0u, 0u);
+    uint4 cur_row[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q) cur_row[q] = make_uint4(0u, 0u, 0u, 0u);
     const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t warps = (int64_t)gridDim.x * (kThreads >> 5);
     for (int64_t vc = warp * s_seg.ch; vc < s_seg.total; vc += warps * s_seg.ch) {
@@ -564,33 +574,38 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
 #pragma unroll
         for (int s0 = 0; s0 < L; s0 += SB) {
             int32_t us[SB];
-            uint4 ra[SB], rb[SB];
+            uint4 ra[SB][VPL], rb[SB][VPL];
 #pragma unroll
             for (int t = 0; t < SB; ++t) {
                 const unsigned src = (unsigned)(grp * L + s0 + t);  // lane owning this step's item
                 us[t] = __shfl_sync(0xffffffffu, cu, src);
                 // items past the range read row 0 and count nothing
                 const int32_t vs_ = max(__shfl_sync(0xffffffffu, cv, src), 0);
-                rb[t] = ldg4(rowbase + (int64_t)vs_ * p.stride);
-                if (UREUSE && us[t] == cur_u)
-                    ra[t] = cur_row;
-                else
-                    ra[t] = ldg4(rowbase + (int64_t)max(us[t], 0) * p.stride);
+                const bool reuse = UREUSE && us[t] == cur_u;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    rb[t][q] = ldg4(rowbase[q] + (int64_t)vs_ * p.stride);
+                    ra[t][q] = reuse ? cur_row[q] : ldg4(rowbase[q] + (int64_t)max(us[t], 0) * p.stride);
+                }
             }
 #pragma unroll
             for (int t = 0; t < SB; ++t) {
-                uint32_t v;
-                if (KIND == BLOOM) {
-                    v = (ok0 ? __popc(ra[t].x & rb[t].x) : 0u) + (ok1 ? __popc(ra[t].y & rb[t].y) : 0u) +
-                        (ok2 ? __popc(ra[t].z & rb[t].z) : 0u) + (ok3 ? __popc(ra[t].w & rb[t].w) : 0u);
-                } else {
-                    v = (ok0 && ra[t].x == rb[t].x) + (ok1 && ra[t].y == rb[t].y) +
-                        (ok2 && ra[t].z == rb[t].z) + (ok3 && ra[t].w == rb[t].w);
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) {
+                    const uint4 a = ra[t][q], b = rb[t][q];
+                    if (KIND == BLOOM) {
+                        v += (ok[q][0] ? __popc(a.x & b.x) : 0u) + (ok[q][1] ? __popc(a.y & b.y) : 0u) +
+                             (ok[q][2] ? __popc(a.z & b.z) : 0u) + (ok[q][3] ? __popc(a.w & b.w) : 0u);
+                    } else {
+                        v += (ok[q][0] && a.x == b.x) + (ok[q][1] && a.y == b.y) + (ok[q][2] && a.z == b.z) +
+                             (ok[q][3] && a.w == b.w);
+                    }
                 }
-                if (kRedux) {
-                    // counts of both 16-lane groups in one reduction (group 1 in the upper half)
+                if (kPack) {
+                    // every group's count in one reduction, group grp in bits [grp kPack, (grp + 1) kPack)
                     const uint32_t r = __reduce_add_sync(0xffffffffu, v << grp_shift);
-                    if ((int)g == s0 + t) c = (r >> grp_shift) & 0xFFFFu;
+                    if ((int)g == s0 + t) c = (r >> grp_shift) & ((1u << kPack) - 1u);
                 } else {
 #pragma unroll
                     for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -599,7 +614,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             }
             if (UREUSE && us[SB - 1] >= 0) {
                 cur_u = us[SB - 1];
-                cur_row = ra[SB - 1];
+#pragma unroll
+                for (int q = 0; q < VPL; ++q) cur_row[q] = ra[SB - 1][q];
             }
         }
 
