@@ -93,87 +93,138 @@ __global__ void k_group_count(const int32_t *__restrict__ row_ptr, const int32_t
 
 // The grouped list: entry i = (eu[i], ev[i]) and the degree sum d_u + d_v, eds[i].
 // off = the scanned counts (group j's row u occupies [off_j[u], off_j[u+1]),
-// off_j = off + j * (n + 1)); group j spans [off_j[0], off_j[n]). The output
-// is cut into chunks of kListChunk entries; a warp takes a chunk, finds the
-// group and the row holding its first entry (a 32-way search over off_j), and
-// walks windows of 32 consecutive rows: each lane locates the window row of
-// its output position with a binary search over the 32 segment ends held in
-// the lanes. Stores are coalesced and each lane has kListUnroll independent
-// loads in flight. Writes at or beyond cap are dropped.
-constexpr int32_t kListChunk = 4096;
+// off_j = off + j * (n + 1)); group j spans [off_j[0], off_j[n]) and only its
+// rows u < R_j = min(n, (j + 1) * 2^shift) can hold entries (u < v).
+//
+// Work is cut by merge path: an item is a row visited or an entry written,
+// group j's items are its R_j rows and its entries, ordered by row with each
+// row followed by its entries, so that D(j, u) = base_j + u + off_j[u]
+// (base_j = R_0 + ... + R_{j-1}) items precede row u of group j. A chunk is
+// kListItems consecutive items: a warp locates both ends (cut) with a
+// 32-way search and walks windows of 32 consecutive rows from the first,
+// each lane finding the window row of its output position by a binary
+// search over the 32 segment ends held in the lanes. A chunk's cost is
+// bounded whether its rows are dense or sparse: where a group's entries
+// thin out (its rows just below R_j), the rows themselves fill the chunk.
+// Stores are coalesced and each lane has kListUnroll independent loads in
+// flight. Entry indices fit in int32 (m <= nnz / 2 < 2^30); item counts may
+// not. Writes at or beyond cap are dropped.
+constexpr int32_t kListItems = 4096;
 constexpr int kListUnroll = 4;
 
-__global__ void __launch_bounds__(256) k_group_lists(const int32_t *__restrict__ row_ptr,
-                                                     const int32_t *__restrict__ col, int32_t n, int32_t groups,
-                                                     const int32_t *__restrict__ upper_off,
-                                                     const int32_t *__restrict__ off,
+struct ListCut {
+    int32_t j, u, e;  // group, first row to walk, first entry
+};
+
+__device__ __forceinline__ int64_t group_rows(int32_t j, int32_t n, int32_t shift) {
+    const int64_t r = (int64_t)(j + 1) << shift;
+    return r < (int64_t)n ? r : (int64_t)n;
+}
+
+// The cuts at items d[0] and d[1] (0 <= d <= total), located together so that
+// their loads overlap. Group: the last j with D(j, 0) <= d (lane j tests
+// group j); row: the largest u in [0, R_j] with u + off_j[u] <= d - base_j.
+__device__ __forceinline__ void list_cuts(const int32_t *__restrict__ off, int32_t n, int32_t shift,
+                                          int32_t groups, const int64_t d[2], ListCut cut[2],
+                                          unsigned lane) {
+    int64_t lbase = 0;
+    for (int32_t i = 0; i < (int32_t)lane && i < groups; ++i) lbase += group_rows(i, n, shift);
+    const int64_t lstart =
+        (int32_t)lane < groups ? lbase + off[(int64_t)lane * ((int64_t)n + 1)] : INT64_MAX;
+    int64_t t[2], lo[2], hi[2];
+    const int32_t *offj[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const unsigned bal = __ballot_sync(0xffffffffu, lstart <= d[s]);  // lane 0 always holds
+        const int j = 31 - __clz((int)bal);
+        cut[s].j = j;
+        t[s] = d[s] - __shfl_sync(0xffffffffu, lbase, j);
+        offj[s] = off + (int64_t)j * ((int64_t)n + 1);
+        lo[s] = 0;
+        hi[s] = group_rows(j, n, shift);
+    }
+    while (hi[0] - lo[0] >= 32 || hi[1] - lo[1] >= 32) {
+        int64_t step[2];
+        bool ok[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            // 32 probes reach past hi: lo + 32 * step > hi
+            step[s] = hi[s] - lo[s] >= 32 ? (hi[s] - lo[s]) / 32 + 1 : 0;
+            const int64_t probe = lo[s] + (int64_t)lane * step[s];
+            ok[s] = step[s] > 0 && probe <= hi[s] && probe + offj[s][probe] <= t[s];
+        }
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (step[s] == 0) continue;  // warp-uniform
+            const int last = 31 - __clz((int)__ballot_sync(0xffffffffu, ok[s] || lane == 0));
+            const int64_t nlo = lo[s] + (int64_t)last * step[s];
+            hi[s] = nlo + step[s] - 1 < hi[s] ? nlo + step[s] - 1 : hi[s];
+            lo[s] = nlo;
+        }
+    }
+    bool ok[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int64_t probe = lo[s] + lane;
+        ok[s] = probe <= hi[s] && probe + offj[s][probe] <= t[s];
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int64_t u = lo[s] + (31 - __clz((int)__ballot_sync(0xffffffffu, ok[s] || lane == 0)));
+        cut[s].u = (int32_t)u;
+        cut[s].e = (int32_t)(t[s] - u);
+    }
+}
+
+__global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restrict__ row_ptr,
+                                                     const int32_t *__restrict__ col, int32_t n, int32_t shift,
+                                                     int32_t groups, const int32_t *__restrict__ off,
                                                      const int32_t *__restrict__ seg_end,
                                                      int32_t *__restrict__ eu, int32_t *__restrict__ ev,
                                                      int32_t *__restrict__ eds, int64_t cap) {
     const unsigned lane = threadIdx.x & 31u;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    int64_t m = upper_off[n];
-    if (m > cap) m = cap;
-    const int64_t chunks = (m + kListChunk - 1) / kListChunk;
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
-        int64_t c0 = c * kListChunk;
-        const int64_t c1 = c0 + kListChunk < m ? c0 + kListChunk : m;
-        while (c0 < c1) {
-            // group of c0: the last j with off_j[0] <= c0 (groups <= 32)
-            const bool gok = (int32_t)lane < groups && (int64_t)off[(int64_t)lane * ((int64_t)n + 1)] <= c0;
-            const int j = 31 - __clz((int)__ballot_sync(0xffffffffu, gok));  // lane 0 always satisfies gok
+    int64_t total = off[(int64_t)(groups - 1) * ((int64_t)n + 1) + n];
+    for (int32_t j = 0; j < groups; ++j) total += group_rows(j, n, shift);
+    const int32_t cap32 = cap < (int64_t)INT32_MAX ? (int32_t)cap : INT32_MAX;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c * kListItems < total; c += warps) {
+        const int64_t d[2] = {c * kListItems, (c + 1) * kListItems < total ? (c + 1) * kListItems : total};
+        ListCut cut[2];
+        list_cuts(off, n, shift, groups, d, cut, lane);
+        for (int32_t j = cut[0].j; j <= cut[1].j; ++j) {
             const int32_t *offj = off + (int64_t)j * ((int64_t)n + 1);
             const int32_t *endj = seg_end + (int64_t)j * n;
-            const int64_t gend = offj[n];
-            const int64_t s1 = c1 < gend ? c1 : gend;
-            // largest u in [0, n-1] with offj[u] <= c0, by a 32-way search
-            int64_t lo = 0, hi = (int64_t)n - 1;
-            while (hi - lo >= 32) {
-                const int64_t step = (hi - lo + 31) / 32;
-                const int64_t probe = lo + (int64_t)lane * step;
-                const bool ok = probe <= hi && offj[probe] <= c0;
-                const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                const int last = 31 - __clz((int)bal);
-                const int64_t nlo = lo + (int64_t)last * step;
-                hi = (nlo + step - 1 < hi) ? nlo + step - 1 : hi;
-                lo = nlo;
-            }
-            {
-                const int64_t probe = lo + lane;
-                const bool ok = probe <= hi && offj[probe] <= c0;
-                const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                lo += 31 - __clz((int)bal);
-            }
-            int64_t u0 = lo;
-            int64_t e = c0;
-            while (e < s1) {
+            int32_t u0 = j == cut[0].j ? cut[0].u : 0;
+            int32_t e = j == cut[0].j ? cut[0].e : offj[0];
+            const int32_t s1 = j == cut[1].j ? cut[1].e : offj[n];
+            while (e < s1 && u0 < n) {
                 // window rows u0 .. u0+31 (lanes past n repeat row n-1)
-                const int64_t ul = u0 + lane < n ? u0 + lane : (int64_t)n - 1;
+                const int32_t ul = u0 + (int32_t)lane < n ? u0 + (int32_t)lane : n - 1;
                 const int32_t off_end = offj[ul + 1];
                 const int32_t se = endj[ul];
                 const int32_t du = row_ptr[ul + 1] - row_ptr[ul];
                 const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
-                const int64_t wend = s1 < (int64_t)last_end ? s1 : (int64_t)last_end;
-                for (int64_t base = e; base < wend; base += 32 * kListUnroll) {
+                const int32_t wend = s1 < last_end ? s1 : last_end;
+                for (int32_t base = e; base < wend; base += 32 * kListUnroll) {
                     // three phases so that all loads of the kListUnroll entries are in flight together:
                     // locate the row and load v, then gather the degrees of v (inside group j's
                     // vertices, so from L2), then store
                     int32_t vs[kListUnroll], rows[kListUnroll], dus[kListUnroll];
 #pragma unroll
                     for (int q = 0; q < kListUnroll; ++q) {
-                        const int64_t ee = base + 32 * q + lane;
+                        const int32_t ee = base + 32 * q + (int32_t)lane;
                         int r = 0;  // window rows whose segment ends at or before ee
 #pragma unroll
                         for (int step = 16; step >= 1; step >>= 1) {
                             const int32_t pr = __shfl_sync(0xffffffffu, off_end, r + step - 1);
-                            if ((int64_t)pr <= ee) r += step;
+                            if (pr <= ee) r += step;
                         }
                         const int rr = r < 31 ? r : 31;
                         const int32_t oe = __shfl_sync(0xffffffffu, off_end, rr);
                         const int32_t sq = __shfl_sync(0xffffffffu, se, rr);
                         rows[q] = rr;
                         dus[q] = __shfl_sync(0xffffffffu, du, rr);
-                        vs[q] = ee < wend ? __ldg(col + (sq - (oe - (int32_t)ee))) : 0;
+                        vs[q] = ee < wend ? __ldg(col + (sq - (oe - ee))) : 0;
                     }
                     int32_t dvs[kListUnroll];
 #pragma unroll
@@ -181,9 +232,9 @@ __global__ void __launch_bounds__(256) k_group_lists(const int32_t *__restrict__
                         dvs[q] = __ldg(row_ptr + vs[q] + 1) - __ldg(row_ptr + vs[q]);
 #pragma unroll
                     for (int q = 0; q < kListUnroll; ++q) {
-                        const int64_t ee = base + 32 * q + lane;
-                        if (ee < wend) {
-                            eu[ee] = (int32_t)(u0 + rows[q]);
+                        const int32_t ee = base + 32 * q + (int32_t)lane;
+                        if (ee < wend && ee < cap32) {
+                            eu[ee] = u0 + rows[q];
                             ev[ee] = vs[q];
                             eds[ee] = dus[q] + dvs[q];
                         }
@@ -192,7 +243,6 @@ __global__ void __launch_bounds__(256) k_group_lists(const int32_t *__restrict__
                 e = wend > e ? wend : e;
                 u0 += 32;
             }
-            c0 = s1 > c0 ? s1 : c1;
         }
     }
 }
@@ -476,11 +526,15 @@ cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32
     if (e != cudaSuccess) return e;
     e = launch_exclusive_scan(cnt, (int64_t)G * count, scratch, s);
     if (e != cudaSuccess || n == 0) return e;
-    const int64_t chunks = (nnz / 2 + kListChunk) / kListChunk;
+    // items: at most G n rows + nnz / 2 + 1 entries
+    const int64_t chunks = ((int64_t)G * n + nnz / 2 + 1 + kListItems - 1) / kListItems;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_lists, 256, 0);
+    if (e != cudaSuccess) return e;
     int64_t grid = (chunks + 7) / 8;
-    if (grid > 8 * device_info().sm_count) grid = 8 * device_info().sm_count;
+    if (grid > (int64_t)per_sm * device_info().sm_count) grid = (int64_t)per_sm * device_info().sm_count;
     if (grid < 1) grid = 1;
-    k_group_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, G, upper_off, cnt, seg,
+    k_group_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, shift, G, cnt, seg,
                                                  reinterpret_cast<int32_t *>(b + L.eu),
                                                  reinterpret_cast<int32_t *>(b + L.ev),
                                                  reinterpret_cast<int32_t *>(b + L.eds), list_cap(nnz));
