@@ -37,16 +37,23 @@ __global__ void k_fill_f64(double *p, size_t count, double value) {
         p[i] = value;
 }
 
-// Per row u: its upper degree |{v in N_u : v > u}| (binary search for u in the
-// sorted row), and the row's upper part cut by the vertex groups: segment j
-// holds the entries with v >> shift == j. cnt[j * (n + 1) + u] = segment
-// length, seg_end[j * n + u] = CSR position one past the segment. Entry n of
-// upper_off and of every cnt row is set to 0, so that the exclusive scans of
-// n + 1 values end with the totals. Rows of up to 32 upper entries find the
-// cuts by walking them; longer rows by binary search.
+// Per row u: its upper degree |{v in N_u : v > u}| and the row's upper part
+// cut by the vertex groups: segment j holds the entries with v >> shift == j.
+// cnt[j * (n + 1) + u] = segment length, seg_end[j * n + u] = CSR position
+// one past the segment, deg[u] = d_u (the list writer gathers it for every
+// entry). Entry n of upper_off and of every cnt row is set to 0, so that the
+// exclusive scans of n + 1 values end with the totals.
+//
+// All cuts are lower bounds in the sorted row: the upper part starts at the
+// first v >= u + 1 and group j - 1 ends at the first v >= j * 2^shift (or at
+// the upper start, if that comes later). The groups' searches share one
+// length sequence, so they run in lockstep, branch-free: every halving step
+// issues the probes of all groups together, and a row costs about log2(d)
+// dependent loads rather than one search after another.
 __global__ void k_group_count(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n,
                               int32_t shift, int32_t groups, int32_t *__restrict__ upper_off,
-                              int32_t *__restrict__ cnt, int32_t *__restrict__ seg_end) {
+                              int32_t *__restrict__ cnt, int32_t *__restrict__ seg_end,
+                              int32_t *__restrict__ deg) {
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u > n) return;
     if (u == n) {
@@ -54,40 +61,45 @@ __global__ void k_group_count(const int32_t *__restrict__ row_ptr, const int32_t
         for (int32_t j = 0; j < groups; ++j) cnt[(int64_t)j * ((int64_t)n + 1) + n] = 0;
         return;
     }
-    int32_t lo = row_ptr[u], hi = row_ptr[u + 1];
-    const int32_t end = hi;
-    while (lo < hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(col + mid) <= (int32_t)u)
-            lo = mid + 1;
-        else
-            hi = mid;
+    const int32_t a = row_ptr[u], end = row_ptr[u + 1];
+    deg[u] = end - a;
+    // thresholds: x_0 = u + 1 (upper start), x_j = j << shift for 1 <= j < groups (group starts)
+    int32_t x[kMaxGroups];
+    int32_t base[kMaxGroups];
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; ++t) {
+        x[t] = t == 0 ? (int32_t)(u + 1) : t << shift;  // < n <= INT32_MAX for t < groups
+        base[t] = a;
     }
+    int32_t len = end - a;
+    while (len > 1) {
+        const int32_t half = len >> 1;
+        int32_t probe[kMaxGroups];
+#pragma unroll
+        for (int t = 0; t < kMaxGroups; ++t)
+            if (t < groups) probe[t] = __ldg(col + base[t] + half);
+#pragma unroll
+        for (int t = 0; t < kMaxGroups; ++t)
+            if (t < groups && probe[t] < x[t]) base[t] += half;
+        len -= half;
+    }
+    if (len == 1) {
+#pragma unroll
+        for (int t = 0; t < kMaxGroups; ++t)
+            if (t < groups && __ldg(col + base[t]) < x[t]) base[t] += 1;
+    }
+    const int32_t lo = base[0];
     upper_off[u] = end - lo;
-    const bool walk = end - lo <= 32;
     int32_t cur = lo;
-    for (int32_t j = 0; j < groups; ++j) {
-        int32_t stop = end;
-        if (j + 1 < groups) {
-            const int64_t bound = (int64_t)(j + 1) << shift;
-            if (walk) {
-                stop = cur;
-                while (stop < end && (int64_t)__ldg(col + stop) < bound) ++stop;
-            } else {
-                int32_t a = cur, b = end;
-                while (a < b) {
-                    const int32_t mid = a + ((b - a) >> 1);
-                    if ((int64_t)__ldg(col + mid) < bound)
-                        a = mid + 1;
-                    else
-                        b = mid;
-                }
-                stop = a;
-            }
+#pragma unroll
+    for (int t = 0; t < kMaxGroups; ++t) {
+        if (t < groups) {
+            int32_t stop = end;
+            if (t + 1 < groups) stop = base[t + 1] > cur ? base[t + 1] : cur;
+            cnt[(int64_t)t * ((int64_t)n + 1) + u] = stop - cur;
+            seg_end[(int64_t)t * n + u] = stop;
+            cur = stop;
         }
-        cnt[(int64_t)j * ((int64_t)n + 1) + u] = stop - cur;
-        seg_end[(int64_t)j * n + u] = stop;
-        cur = stop;
     }
 }
 
@@ -176,10 +188,10 @@ __device__ __forceinline__ void list_cuts(const int32_t *__restrict__ off, int32
     }
 }
 
-__global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restrict__ row_ptr,
-                                                     const int32_t *__restrict__ col, int32_t n, int32_t shift,
+__global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restrict__ col, int32_t n, int32_t shift,
                                                      int32_t groups, const int32_t *__restrict__ off,
                                                      const int32_t *__restrict__ seg_end,
+                                                     const int32_t *__restrict__ deg,
                                                      int32_t *__restrict__ eu, int32_t *__restrict__ ev,
                                                      int32_t *__restrict__ eds, int64_t cap) {
     const unsigned lane = threadIdx.x & 31u;
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restric
                 const int32_t ul = u0 + (int32_t)lane < n ? u0 + (int32_t)lane : n - 1;
                 const int32_t off_end = offj[ul + 1];
                 const int32_t se = endj[ul];
-                const int32_t du = row_ptr[ul + 1] - row_ptr[ul];
+                const int32_t du = deg[ul];
                 const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
                 const int32_t wend = s1 < last_end ? s1 : last_end;
                 for (int32_t base = e; base < wend; base += 32 * kListUnroll) {
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restric
                     int32_t dvs[kListUnroll];
 #pragma unroll
                     for (int q = 0; q < kListUnroll; ++q)
-                        dvs[q] = __ldg(row_ptr + vs[q] + 1) - __ldg(row_ptr + vs[q]);
+                        dvs[q] = __ldg(deg + vs[q]);
 #pragma unroll
                     for (int q = 0; q < kListUnroll; ++q) {
                         const int32_t ee = base + 32 * q + (int32_t)lane;
@@ -433,7 +445,7 @@ void launch_fill_f64(double *p, size_t count, double value, cudaStream_t s) {
 static int64_t scan_tiles(int64_t count) { return (count + kScanTile - 1) / kScanTile; }
 
 // Index layout: upper_off [n+1] | scan scratch | cnt / offsets [G (n+1)] |
-// segment ends [G n] | eu | ev | eds [cap each], where cap = nnz / 2 + 1
+// segment ends [G n] | degrees [n] | eu | ev | eds [cap each], where cap = nnz / 2 + 1
 // bounds m for a symmetric CSR (m = nnz / 2). For a CSR that is not
 // symmetric the lists are cut at cap (consumers read at most cap edges);
 // pg_validate_csr detects such graphs.
@@ -455,7 +467,7 @@ static int32_t group_count(int32_t n, int32_t shift) {
 
 namespace {
 struct IndexLayout {
-    size_t scratch, cnt, seg, eu, ev, eds, total;
+    size_t scratch, cnt, seg, deg, eu, ev, eds, total;
 };
 IndexLayout index_layout(int32_t n, int64_t nnz) {
     const int64_t count = (int64_t)n + 1;
@@ -468,6 +480,8 @@ IndexLayout index_layout(int32_t n, int64_t nnz) {
     o += round_up(sizeof(int32_t) * (size_t)G * (size_t)count, 256);
     L.seg = o;
     o += round_up(sizeof(int32_t) * (size_t)G * (size_t)(n > 0 ? n : 1), 256);
+    L.deg = o;
+    o += round_up(sizeof(int32_t) * (size_t)(n > 0 ? n : 1), 256);
     const size_t lb = round_up(sizeof(int32_t) * (size_t)list_cap(nnz), 256);
     L.eu = o;
     L.ev = o + lb;
@@ -520,7 +534,9 @@ cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32
     int32_t *scratch = reinterpret_cast<int32_t *>(b + L.scratch);
     int32_t *cnt = reinterpret_cast<int32_t *>(b + L.cnt);
     int32_t *seg = reinterpret_cast<int32_t *>(b + L.seg);
-    k_group_count<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(row_ptr, col, n, shift, G, upper_off, cnt, seg);
+    int32_t *deg = reinterpret_cast<int32_t *>(b + L.deg);
+    k_group_count<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(row_ptr, col, n, shift, G, upper_off, cnt, seg,
+                                                                 deg);
     note_launch();
     cudaError_t e = launch_exclusive_scan(upper_off, count, scratch, s);
     if (e != cudaSuccess) return e;
@@ -534,7 +550,7 @@ cudaError_t launch_upper_index(const int32_t *row_ptr, const int32_t *col, int32
     int64_t grid = (chunks + 7) / 8;
     if (grid > (int64_t)per_sm * device_info().sm_count) grid = (int64_t)per_sm * device_info().sm_count;
     if (grid < 1) grid = 1;
-    k_group_lists<<<(unsigned)grid, 256, 0, s>>>(row_ptr, col, n, shift, G, cnt, seg,
+    k_group_lists<<<(unsigned)grid, 256, 0, s>>>(col, n, shift, G, cnt, seg, deg,
                                                  reinterpret_cast<int32_t *>(b + L.eu),
                                                  reinterpret_cast<int32_t *>(b + L.ev),
                                                  reinterpret_cast<int32_t *>(b + L.eds), list_cap(nnz));
