@@ -84,7 +84,7 @@ __device__ __forceinline__ void vertex_params(const BatchMap &bm, int64_t v, uin
 //     k_bloom_hub.
 constexpr int32_t kLaneRow = 32;
 
-template <int kMaxWords32, bool LANE>
+template <int kMaxWords32, bool LANE, int B>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int32_t n, uint32_t l,
     uint32_t b, uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t hub_threshold,
@@ -98,6 +98,10 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
     uint32_t *lf = lane_filters + (size_t)warp * words32 * 32 + lane;
     if (threadIdx.x < 16) pre_s[threadIdx.x] = fmix_pre(hash_seed(seed, threadIdx.x));
     for (int t = lane; t < words32; t += 32) f[t] = 0u;
+    // with a compile-time hash count B, the seeds' pre-images live in registers
+    uint32_t pre_b[B > 0 ? B : 1];
+#pragma unroll
+    for (int i = 0; i < (B > 0 ? B : 1); ++i) pre_b[i] = fmix_pre(hash_seed(seed, (uint32_t)i));
     __syncthreads();
     HubList hubs = hub_list(hub_base);
     const int64_t warps_total = (int64_t)gridDim.x * (kBuildThreads / 32);
@@ -112,11 +116,27 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
         const bool mine = LANE && (int)lane < cnt && my_e - my_a <= kLaneRow;
         if (mine) {
             for (int w = 0; w < words32; ++w) lf[w * 32] = 0u;
-            for (int32_t j = my_a; j < my_e; ++j) {
-                const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - my_id0));
-                for (uint32_t i = 0; i < my_b; ++i) {
-                    const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
-                    lf[(p >> 5) * 32] |= 1u << (p & 31u);
+            // eight ids in flight per step
+            for (int32_t j = my_a; j < my_e; j += 8) {
+                int32_t xs[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) xs[q] = j + q < my_e ? __ldg(col + j + q) : 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (j + q >= my_e) break;
+                    const uint32_t px = fmix_pre((uint32_t)(xs[q] - my_id0));
+                    if (B > 0) {
+#pragma unroll
+                        for (int i = 0; i < B; ++i) {
+                            const uint32_t p = bit_pos(hash_pre(px, pre_b[i]), l);
+                            lf[(p >> 5) * 32] |= 1u << (p & 31u);
+                        }
+                    } else {
+                        for (uint32_t i = 0; i < my_b; ++i) {
+                            const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                            lf[(p >> 5) * 32] |= 1u << (p & 31u);
+                        }
+                    }
                 }
             }
             uint4 *row4 = reinterpret_cast<uint4 *>(data + (v0 + lane) * stride);
@@ -144,10 +164,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
             } else if (deg > 0) {
                 if ((int32_t)lane < deg) {
                     const uint32_t px = fmix_pre((uint32_t)(x - id0));
+                    if (B > 0) {
+#pragma unroll
+                        for (int i = 0; i < B; ++i) {
+                            const uint32_t p = bit_pos(hash_pre(px, pre_b[i]), l);
+                            atomicOr(&f[p >> 5], 1u << (p & 31u));
+                        }
+                    } else {
 #pragma unroll 4
-                    for (uint32_t i = 0; i < bv; ++i) {
-                        const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
-                        atomicOr(&f[p >> 5], 1u << (p & 31u));
+                        for (uint32_t i = 0; i < bv; ++i) {
+                            const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                            atomicOr(&f[p >> 5], 1u << (p & 31u));
+                        }
                     }
                 }
                 // longer rows: four 32-id loads in flight before hashing them
@@ -162,10 +190,18 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
                     for (int q = 0; q < kBloomUnroll; ++q) {
                         if (j0 + 32 * q + (int32_t)lane >= e) continue;
                         const uint32_t px = fmix_pre((uint32_t)(xs[q] - id0));
+                        if (B > 0) {
+#pragma unroll
+                            for (int i = 0; i < B; ++i) {
+                                const uint32_t p = bit_pos(hash_pre(px, pre_b[i]), l);
+                                atomicOr(&f[p >> 5], 1u << (p & 31u));
+                            }
+                        } else {
 #pragma unroll 4
-                        for (uint32_t i = 0; i < bv; ++i) {
-                            const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
-                            atomicOr(&f[p >> 5], 1u << (p & 31u));
+                            for (uint32_t i = 0; i < bv; ++i) {
+                                const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                                atomicOr(&f[p >> 5], 1u << (p & 31u));
+                            }
                         }
                     }
                 }
@@ -187,45 +223,69 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_warp(
 }
 
 // Hub chunks: the block ORs its chunk's bits into a shared filter, then
-// merges it into the row with 64-bit global atomicOr.
+// merges it into the row with 64-bit global atomicOr. Each block takes a
+// contiguous range of chunk tickets (the chunks cost the same, so the ranges
+// are balanced) and finds the owning hub record once, then steps through the
+// records as the tickets pass their first chunks. Each thread keeps
+// kHubUnroll loads of ids in flight before hashing them.
+constexpr int kHubUnroll = 8;
+
 template <int kMaxWords32>
 __global__ void __launch_bounds__(kBuildThreads) k_bloom_hub(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, uint32_t l, uint32_t b,
     uint32_t seed, uint8_t *__restrict__ data, int64_t stride, int32_t chunk, int32_t *hub_base,
     BatchMap bm) {
     __shared__ uint32_t f[kMaxWords32];
-    __shared__ int2 task;
     __shared__ uint32_t pre_s[16];
     if (threadIdx.x < 16) pre_s[threadIdx.x] = fmix_pre(hash_seed(seed, threadIdx.x));
-    __syncthreads();
     HubList hubs = hub_list(hub_base);
     const unsigned long long packed = *reinterpret_cast<volatile unsigned long long *>(hubs.packed);
     const int count = (int)(packed >> 32);
     const int64_t total = (int64_t)(packed & 0xffffffffull);
     const int words32 = (int)(stride >> 2);
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int h = hub_find(hubs.rec, count, t);
-            task = make_int2(hubs.rec[h].x, (int32_t)(t - hubs.rec[h].y));
+    const int64_t t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+    if (t0 >= t1) return;  // the whole block
+    int h = hub_find(hubs.rec, count, t0);
+    int2 rec = hubs.rec[h];
+    int64_t next = h + 1 < count ? (int64_t)hubs.rec[h + 1].y : INT64_MAX;
+    int32_t a = row_ptr[rec.x], e = row_ptr[rec.x + 1];
+    uint32_t bv = b;
+    int32_t id0 = 0;
+    vertex_params(bm, rec.x, bv, id0);
+    for (int64_t t = t0; t < t1; ++t) {
+        while (t >= next) {
+            ++h;
+            rec = hubs.rec[h];
+            next = h + 1 < count ? (int64_t)hubs.rec[h + 1].y : INT64_MAX;
+            a = row_ptr[rec.x];
+            e = row_ptr[rec.x + 1];
+            bv = b;
+            id0 = 0;
+            vertex_params(bm, rec.x, bv, id0);
         }
         for (int q = threadIdx.x; q < words32; q += blockDim.x) f[q] = 0u;
         __syncthreads();
-        const int32_t v = task.x;
-        const int32_t a = row_ptr[v], e = row_ptr[v + 1];
-        const int32_t c0 = a + task.y * chunk;
+        const int32_t c0 = a + (int32_t)(t - rec.y) * chunk;
         const int32_t c1 = min(e, c0 + chunk);
-        uint32_t bv = b;
-        int32_t id0 = 0;
-        vertex_params(bm, v, bv, id0);
-        for (int32_t j = c0 + threadIdx.x; j < c1; j += blockDim.x) {
-            const uint32_t px = fmix_pre((uint32_t)(__ldg(col + j) - id0));
-            for (uint32_t i = 0; i < bv; ++i) {
-                const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
-                atomicOr(&f[p >> 5], 1u << (p & 31u));
+        for (int32_t j0 = c0 + (int32_t)threadIdx.x; j0 < c1; j0 += kHubUnroll * (int32_t)blockDim.x) {
+            int32_t xs[kHubUnroll];
+#pragma unroll
+            for (int q = 0; q < kHubUnroll; ++q) {
+                const int32_t j = j0 + q * (int32_t)blockDim.x;
+                xs[q] = j < c1 ? __ldg(col + j) : 0;
+            }
+#pragma unroll
+            for (int q = 0; q < kHubUnroll; ++q) {
+                if (j0 + q * (int32_t)blockDim.x >= c1) continue;
+                const uint32_t px = fmix_pre((uint32_t)(xs[q] - id0));
+                for (uint32_t i = 0; i < bv; ++i) {
+                    const uint32_t p = bit_pos(hash_pre(px, pre_s[i]), l);
+                    atomicOr(&f[p >> 5], 1u << (p & 31u));
+                }
             }
         }
         __syncthreads();
-        unsigned long long *row = reinterpret_cast<unsigned long long *>(data + (int64_t)v * stride);
+        unsigned long long *row = reinterpret_cast<unsigned long long *>(data + (int64_t)rec.x * stride);
         for (int q = threadIdx.x; q < words32 / 2; q += blockDim.x) {
             unsigned long long w = (unsigned long long)f[2 * q] | ((unsigned long long)f[2 * q + 1] << 32);
             if (w) atomicOr(row + q, w);
@@ -237,17 +297,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_bloom_hub(
 // --------------------------------------------------------------- k-Hash --
 // Lane r owns hash indices i = r + t*(32/P) (t < KPL); with P > 1 the warp
 // splits into P partitions that walk disjoint element subsets and are
-// min-combined at the end. Elements are loaded 32 at a time (coalesced) and
-// broadcast by shuffles.
+// min-combined at the end. Elements are loaded 32 at a time (coalesced, the
+// next 32 in flight while the current ones are hashed) and broadcast by
+// shuffles.
 template <int KPL, int P>
 __device__ __forceinline__ void khash_slice(const int32_t *__restrict__ col, int32_t a, int32_t e,
                                             const uint32_t (&pre_s)[KPL], uint32_t (&mn)[KPL]) {
     constexpr int kLanesPerPart = 32 / P;
     const unsigned lane = lane_id();
     const unsigned part = lane / kLanesPerPart;
+    int32_t nx = (a + (int32_t)lane < e) ? __ldg(col + a + lane) : 0;
     for (int32_t base = a; base < e; base += 32) {
         const int32_t cnt = min(32, e - base);
-        const uint32_t px_mine = (lane < (unsigned)cnt) ? fmix_pre((uint32_t)__ldg(col + base + lane)) : 0u;
+        const uint32_t px_mine = (lane < (unsigned)cnt) ? fmix_pre((uint32_t)nx) : 0u;
+        // the next 32 ids in flight while these are hashed
+        nx = (base + 32 + (int32_t)lane < e) ? __ldg(col + base + 32 + lane) : 0;
         if (P == 1 && cnt == 32) {
             // a full chunk, two entries per step: one three-input min takes both hashes, and no
             // per-entry bound check
@@ -313,13 +377,16 @@ __global__ void __launch_bounds__(kBuildThreads) k_khash_warp(
     }
 }
 
+// Hub chunks of 2048 ids: the block's warps take equal slices, min-combine
+// them in shared memory and merge into the row with global atomicMin. As in
+// k_bloom_hub, each block takes a contiguous range of chunk tickets and
+// locates the owning hub record once.
 template <int KPL, int P>
 __global__ void __launch_bounds__(kBuildThreads) k_khash_hub(
     const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, uint32_t k, uint32_t seed,
     uint8_t *__restrict__ data, int64_t stride, int32_t chunk, int32_t *hub_base) {
     constexpr int kLanesPerPart = 32 / P;
     __shared__ uint32_t smin[256];
-    __shared__ int2 task;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned slot = lane % kLanesPerPart;
     uint32_t pre_s[KPL];
@@ -333,16 +400,23 @@ __global__ void __launch_bounds__(kBuildThreads) k_khash_hub(
     const int count = (int)(packed >> 32);
     const int64_t total = (int64_t)(packed & 0xffffffffull);
     constexpr int kWarps = kBuildThreads / 32;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int h = hub_find(hubs.rec, count, t);
-            task = make_int2(hubs.rec[h].x, (int32_t)(t - hubs.rec[h].y));
+    const int64_t t0 = total * blockIdx.x / gridDim.x, t1 = total * (blockIdx.x + 1) / gridDim.x;
+    if (t0 >= t1) return;  // the whole block
+    int h = hub_find(hubs.rec, count, t0);
+    int2 rec = hubs.rec[h];
+    int64_t next = h + 1 < count ? (int64_t)hubs.rec[h + 1].y : INT64_MAX;
+    int32_t a = row_ptr[rec.x], e = row_ptr[rec.x + 1];
+    for (int64_t t = t0; t < t1; ++t) {
+        while (t >= next) {
+            ++h;
+            rec = hubs.rec[h];
+            next = h + 1 < count ? (int64_t)hubs.rec[h + 1].y : INT64_MAX;
+            a = row_ptr[rec.x];
+            e = row_ptr[rec.x + 1];
         }
         for (int q = threadIdx.x; q < (int)k; q += blockDim.x) smin[q] = kEmpty;
         __syncthreads();
-        const int32_t v = task.x;
-        const int32_t a = row_ptr[v], e = row_ptr[v + 1];
-        const int32_t c0 = a + task.y * chunk;
+        const int32_t c0 = a + (int32_t)(t - rec.y) * chunk;
         const int32_t c1 = min(e, c0 + chunk);
         // warp w takes the w-th of kWarps equal slices of the chunk
         const int32_t len = c1 - c0;
@@ -364,7 +438,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_khash_hub(
             }
         }
         __syncthreads();
-        uint32_t *row = reinterpret_cast<uint32_t *>(data + (int64_t)v * stride);
+        uint32_t *row = reinterpret_cast<uint32_t *>(data + (int64_t)rec.x * stride);
         for (int q = threadIdx.x; q < (int)k; q += blockDim.x)
             if (smin[q] != kEmpty) atomicMin(row + q, smin[q]);
         __syncthreads();
@@ -510,17 +584,22 @@ cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32
     const BatchMap bm = bmap ? *bmap : BatchMap{};
     launch_fill_u64(reinterpret_cast<uint64_t *>(hub_base), 2, 0, s);
     const int grid = build_grid(n);
-    const int hub_grid = device_info().sm_count * 4;
+    const int hub_grid = device_info().sm_count * 8;
     if (stride <= 128) {
         // lane-private filters for short rows: words x 32 lanes x warps
         const size_t lane_smem = (size_t)(stride / 4) * 32 * (kBuildThreads / 32) * 4;
-        k_bloom_warp<32, true><<<grid, kBuildThreads, lane_smem, s>>>(row_ptr, col, n, l, b, seed, data, stride,
-                                                                      kBloomHub, kBloomChunk, hub_base, bm);
+        // one graph with two hash functions (the common case): the count fixed at compile time
+        if (!bm.gid && b == 2)
+            k_bloom_warp<32, true, 2><<<grid, kBuildThreads, lane_smem, s>>>(
+                row_ptr, col, n, l, b, seed, data, stride, kBloomHub, kBloomChunk, hub_base, bm);
+        else
+            k_bloom_warp<32, true, 0><<<grid, kBuildThreads, lane_smem, s>>>(
+                row_ptr, col, n, l, b, seed, data, stride, kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<32><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
                                                            kBloomChunk, hub_base, bm);
         note_launch(2);
     } else {
-        k_bloom_warp<256, false><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
+        k_bloom_warp<256, false, 0><<<grid, kBuildThreads, 0, s>>>(row_ptr, col, n, l, b, seed, data, stride,
                                                                 kBloomHub, kBloomChunk, hub_base, bm);
         k_bloom_hub<256><<<hub_grid, kBuildThreads, 0, s>>>(row_ptr, col, l, b, seed, data, stride,
                                                             kBloomChunk, hub_base, bm);
@@ -536,7 +615,7 @@ static void khash_pair(const int32_t *row_ptr, const int32_t *col, int32_t n, ui
     k_khash_warp<KPL, P><<<build_grid(n), kBuildThreads, 0, s>>>(row_ptr, col, n, k, seed, data,
                                                                  stride, kKhashHub, kKhashChunk,
                                                                  hub_base);
-    k_khash_hub<KPL, P><<<device_info().sm_count * 4, kBuildThreads, 0, s>>>(
+    k_khash_hub<KPL, P><<<device_info().sm_count * 5, kBuildThreads, 0, s>>>(
         row_ptr, col, k, seed, data, stride, kKhashChunk, hub_base);
     note_launch(2);
 }
