@@ -15,6 +15,9 @@
  *             unless a comment says HOST. The library allocates no device
  *             memory; calls that need scratch take a caller-provided
  *             workspace whose size the matching *_bytes function returns.
+ *             A workspace is in use until the call's work on its stream
+ *             has finished: calls that may run at the same time (on
+ *             different streams) need separate workspaces.
  *   Streams   Every call is stream-ordered on `stream` (NULL = the legacy
  *             default stream) and returns without synchronising it, except
  *             pg_server_* / pg_poll, which are documented separately.
