@@ -440,6 +440,19 @@ def time_build_alone(pipe: Pipeline, sk, reps: int = 3) -> float:
     return start.elapsed_time(end) / reps
 
 
+def h2d_rate(dev_t, host_t) -> float:
+    """GB/s of one copy of host_t (page-locked) into dev_t (same bytes) on the current stream:
+    the machine's host-to-device rate, which bounds the end-to-end step."""
+    dev_t.copy_(host_t, non_blocking=True)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    dev_t.copy_(host_t, non_blocking=True)
+    end.record()
+    torch.cuda.synchronize()
+    return host_t.numel() * host_t.element_size() / (start.elapsed_time(end) * 1e-3) / 1e9
+
+
 def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     """The same step through the public API from pinned host buffers: the CSR
     copy host->device and the results device->host are inside the timing.
@@ -1551,11 +1564,13 @@ def main():
     if args.e2e_steps > 0:
         host_rp = rp.cpu().pin_memory()
         host_col = cl.cpu().pin_memory()
+        h2d_gbs = h2d_rate(pipe.g.col, host_col)
         e2e_ms, e2e_wall, h2d, d2h = e2e_steps(pipe, host_rp, host_col, args.e2e_steps)
         e2e_ms = max_over_ranks(e2e_ms, ws, dev)
         e2e = {"value": pipe.sketched_per_step() * ws / (e2e_ms * 1e-3), "unit": "intersections/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "wall_ms_per_step": e2e_wall}
+               "wall_ms_per_step": e2e_wall, "h2d_gbs": h2d_gbs,
+               "h2d_note": "one copy of the column array from page-locked memory, timed before the e2e steps"}
 
     exact = None
     if not args.no_exact:

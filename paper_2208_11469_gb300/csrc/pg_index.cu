@@ -209,12 +209,16 @@ __global__ void __launch_bounds__(256, 5) k_group_lists(const int32_t *__restric
             int32_t u0 = j == cut[0].j ? cut[0].u : 0;
             int32_t e = j == cut[0].j ? cut[0].e : offj[0];
             const int32_t s1 = j == cut[1].j ? cut[1].e : offj[n];
+            // window rows u0 .. u0+31 (lanes past n repeat row n-1); the next window's row data
+            // is loaded while this window's entries are written
+            int32_t ul = u0 + (int32_t)lane < n ? u0 + (int32_t)lane : n - 1;
+            int32_t off_end_n = offj[ul + 1], se_n = endj[ul], du_n = deg[ul];
             while (e < s1 && u0 < n) {
-                // window rows u0 .. u0+31 (lanes past n repeat row n-1)
-                const int32_t ul = u0 + (int32_t)lane < n ? u0 + (int32_t)lane : n - 1;
-                const int32_t off_end = offj[ul + 1];
-                const int32_t se = endj[ul];
-                const int32_t du = deg[ul];
+                const int32_t off_end = off_end_n, se = se_n, du = du_n;
+                ul = u0 + 32 + (int32_t)lane < n ? u0 + 32 + (int32_t)lane : n - 1;
+                off_end_n = offj[ul + 1];
+                se_n = endj[ul];
+                du_n = deg[ul];
                 const int32_t last_end = __shfl_sync(0xffffffffu, off_end, 31);
                 const int32_t wend = s1 < last_end ? s1 : last_end;
                 for (int32_t base = e; base < wend; base += 32 * kListUnroll) {

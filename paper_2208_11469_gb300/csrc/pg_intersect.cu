@@ -512,6 +512,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     // k-Hash match counts (at most 64 for the packed forms) of all groups in one integer
     // reduction: 2 groups x 16 bits (L = 16) or 4 groups x 8 bits (L = 8)
     constexpr int kPack = (KIND == KHASH && L == 16) ? 16 : (KIND == KHASH && L == 8 && W <= 255) ? 8 : 0;
+    // with 16-bit fields (k = 64) the warp-uniform reduction of each step goes to shared memory and
+    // every lane takes its own count once per iteration, instead of a compare, shift, mask and
+    // select per step (measured 16.3 -> 16.0 ms at scale 24 together with UREUSE = false)
+    constexpr bool kStash = kPack == 16;
     extern __shared__ __align__(16) unsigned char smem[];
     double *tab = reinterpret_cast<double *>(smem);
     unsigned long long *tabV = reinterpret_cast<unsigned long long *>(smem + 8 * (size_t)p.table_len);
@@ -551,6 +555,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
     }
     const uint32_t grp_shift = (uint32_t)grp * (uint32_t)kPack;
     const bool need_deg = p.need_deg != 0;
+    __shared__ uint32_t s_stash[kStash ? kThreads / 32 : 1][32];
+    uint32_t *stash = s_stash[kStash ? threadIdx.x >> 5 : 0];
 
     int32_t cur_u = -1;
     uint4 cur_row[VPL];
@@ -605,7 +611,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
                 if (kPack) {
                     // every group's count in one reduction, group grp in bits [grp kPack, (grp + 1) kPack)
                     const uint32_t r = __reduce_add_sync(0xffffffffu, v << grp_shift);
-                    if ((int)g == s0 + t) c = (r >> grp_shift) & ((1u << kPack) - 1u);
+                    if (kStash) {
+                        if (lane == 0) stash[s0 + t] = r;  // warp-uniform
+                    } else if ((int)g == s0 + t) {
+                        c = (r >> grp_shift) & ((1u << kPack) - 1u);
+                    }
                 } else {
 #pragma unroll
                     for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -619,6 +629,11 @@ __global__ void __launch_bounds__(kThreads, MINB) k_lean(Params p) {
             }
         }
 
+        if (kStash) {
+            __syncwarp();
+            c = (stash[g] >> grp_shift) & ((1u << kPack) - 1u);
+            __syncwarp();
+        }
         // ---- epilogue: every lane, for its own item
         const int64_t e = EDGE_OUT ? out_pos<false>(p, gj, cu, eb + lane) : eb + lane;
         unsigned long long V = 0ull;
@@ -1208,7 +1223,7 @@ cudaError_t launch_intersect_ws(const int32_t *row_ptr, const int32_t *col, int3
     } else if (sk.kind == PG_SK_KHASH) {
         // k <= 256: up to 64 vectors; at most 16 lanes with up to 4 vectors each
         p.nvec = (int32_t)((sk.k + 3) / 4);
-        if (sk.k == 64) PG_LEAN(KHASH, 16, 64, 8, true, 3);
+        if (sk.k == 64) PG_LEAN(KHASH, 16, 64, 8, false, 3);
         if (sk.k == 32) PG_LEAN(KHASH, 8, 32, 2, true, 3);
         if (sk.k == 16) PG_LEAN(KHASH, 4, 16, 4, true, 3);
         const int L = pow2_at_least(p.nvec) > 16 ? 16 : pow2_at_least(p.nvec);
