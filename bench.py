@@ -216,11 +216,39 @@ def alu_peak(sm_mhz):
 PASS_SOURCES = ("pg_intersect.cu", "pg_internal.cuh", "pg_index.cu")
 
 
+def code_only(src: str) -> str:
+    """C++/CUDA source without its comments, whitespace runs collapsed to one
+    space (string and character literals kept as they are), so that the
+    fingerprint changes with the code and not with its comments."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_fingerprint() -> str:
-    """sha256 over the pass sources, in PASS_SOURCES order."""
+    """sha256 over the code of the pass sources (comments removed), in
+    PASS_SOURCES order."""
     h = hashlib.sha256()
     for f in PASS_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2208_11469_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2208_11469_gb300", "csrc", f), encoding="utf-8").read()
+        h.update(code_only(src).encode("utf-8"))
     return h.hexdigest()
 
 

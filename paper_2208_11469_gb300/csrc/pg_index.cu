@@ -118,6 +118,9 @@ __global__ void k_group_count(const int32_t *__restrict__ row_ptr, const int32_t
 // search over the 32 segment ends held in the lanes. A chunk's cost is
 // bounded whether its rows are dense or sparse: where a group's entries
 // thin out (its rows just below R_j), the rows themselves fill the chunk.
+// d_v is gathered from the degree array the count kernel writes (group j's
+// slice, so from L2), and the next window's row data (segment end offsets,
+// segment ends, degrees) is loaded while the current window is written.
 // Stores are coalesced and each lane has kListUnroll independent loads in
 // flight. Entry indices fit in int32 (m <= nnz / 2 < 2^30); item counts may
 // not. Writes at or beyond cap are dropped.

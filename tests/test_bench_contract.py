@@ -85,3 +85,18 @@ def test_oracle_leg_samples_the_whole_graph():
     rate, T = leg._rate(2.0, 1.0, 100, 1000)
     assert T == pytest.approx(2.0 * leg.n / 100 + 1.0 * leg.m / 1000)
     assert rate == pytest.approx(2 * leg.m / T)
+
+
+def test_source_fingerprint_ignores_comments_only():
+    """The traffic gate's fingerprint follows the code of the pass sources:
+    comments and whitespace do not move it, any code token does, and comment
+    markers inside string or character literals are code."""
+    import bench
+    a = "int f(int x) { return x + 1; } // add one\n"
+    b = "/* a comment */ int  f(int x)\n{ return x + 1; }\n"
+    c = "int f(int x) { return x + 2; }\n"
+    assert bench.code_only(a) == bench.code_only(b)
+    assert bench.code_only(a) != bench.code_only(c)
+    s = 'const char *u = "http://x"; char q = \'/\';'
+    assert bench.code_only(s) == s
+    assert len(bench.source_fingerprint()) == 64
