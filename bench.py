@@ -324,11 +324,12 @@ class Pipeline:
                 out.append(sk)
         return out
 
-    def step(self, ev=None, builds=True, csr_stream=None):
+    def step(self, ev=None, builds=True, csr_stream=None, prebuilt=()):
         """One pass of the hot path. ev: optional dict name -> (start, end) events.
         builds=False: the sketches are already built (by upload_build);
-        csr_stream: the stream that uploaded the CSR (the index then waits for
-        it alone, beside the builds' tail on the launching stream).
+        prebuilt: ids of the sketches already built (the others are built here);
+        csr_stream: the stream that uploaded the CSR (the side stream then waits
+        for it alone, beside the builds' tail on the launching stream).
 
         The edge index and the sketch builds depend only on the CSR, so they
         run on two streams: the index and then the Bloom builds (bound by memory
@@ -351,7 +352,7 @@ class Pipeline:
                 pg.build_minhash(g, sk.kind, sk.k, sk.seed, out=sk, workspace=ws)
             mark("build_" + name, 1, stream)
 
-        todo, seen = [], set() if builds else {id(sk) for _, sk, _ in self.passes}
+        todo, seen = [], set(prebuilt) if builds else {id(sk) for _, sk, _ in self.passes}
         for name, sk, est in self.passes:
             if id(sk) not in seen:
                 seen.add(id(sk))
@@ -485,10 +486,10 @@ def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     """The same step through the public API from pinned host buffers: the CSR
     copy host->device and the results device->host are inside the timing.
     The upload goes through pg_upload_build, which copies the CSR in row
-    chunks on a copy stream and builds the sketches of each chunk while the
-    next one is copied; the edge index starts on a side stream as soon as the
-    last chunk has landed (beside the remaining builds), and the passes
-    follow both."""
+    chunks on a copy stream and builds the MinHash sketches of each chunk
+    while the next one is copied; as soon as the last chunk has landed the
+    edge index and then the Bloom build run on a side stream (beside the
+    remaining MinHash builds), and the passes follow both."""
     pg = pipe.pg
     g = pipe.g
     d2h = []
@@ -500,11 +501,11 @@ def e2e_steps(pipe: Pipeline, host_rp, host_col, steps: int):
     t0 = time.perf_counter()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record()
-    sketches = pipe.sketches()
+    chunked = [sk for sk in pipe.sketches() if sk.kind != pg.SK_BLOOM]
     copy = torch.cuda.Stream(device=g.device)
     for _ in range(steps):
-        pg.upload_build(g, host_rp, host_col, sketches, workspace=pipe.build_ws, copy_stream=copy)
-        pipe.step(builds=False, csr_stream=copy)
+        pg.upload_build(g, host_rp, host_col, chunked, workspace=pipe.build_ws, copy_stream=copy)
+        pipe.step(csr_stream=copy, prebuilt={id(sk) for sk in chunked})
         for dev_t, host_t in d2h:
             host_t.copy_(dev_t, non_blocking=True)
     end.record()
