@@ -148,7 +148,9 @@ cudaError_t launch_validate(const int32_t *row_ptr, const int32_t *col, int32_t 
 
 // Per-vertex parameters of batched graphs (pg_batch.cu): global vertex of local
 // vertex v = v_base + v, its graph gid[.], the graph's first global id voff[g]
-// and hash count b_of[g]. gid == nullptr: a single graph.
+// and hash count b_of[g]. gid == nullptr: a single graph. A batched build
+// launch covers whole graphs of one bucket, so b_of[g] equals the launch's b
+// for every graph in it (launch_build_bloom relies on this).
 struct BatchMap {
     const int32_t *gid;
     const int32_t *voff;

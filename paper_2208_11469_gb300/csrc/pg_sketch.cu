@@ -588,9 +588,13 @@ cudaError_t launch_build_bloom(const int32_t *row_ptr, const int32_t *col, int32
     if (stride <= 128) {
         // lane-private filters for short rows: words x 32 lanes x warps
         const size_t lane_smem = (size_t)(stride / 4) * 32 * (kBuildThreads / 32) * 4;
-        // one graph with two hash functions (the common case): the count fixed at compile time
-        if (!bm.gid && b == 2)
+        // the hash count fixed at compile time for b = 1 and b = 2 (a batched launch covers whole
+        // graphs of one bucket, which all have the bucket's b)
+        if (b == 2)
             k_bloom_warp<32, true, 2><<<grid, kBuildThreads, lane_smem, s>>>(
+                row_ptr, col, n, l, b, seed, data, stride, kBloomHub, kBloomChunk, hub_base, bm);
+        else if (b == 1)
+            k_bloom_warp<32, true, 1><<<grid, kBuildThreads, lane_smem, s>>>(
                 row_ptr, col, n, l, b, seed, data, stride, kBloomHub, kBloomChunk, hub_base, bm);
         else
             k_bloom_warp<32, true, 0><<<grid, kBuildThreads, lane_smem, s>>>(
