@@ -267,7 +267,8 @@ struct BuildParams {
     int32_t chunk;
 };
 
-template <int WORDS>  // 32-bit words per stored row (stride / 4)
+// B: the bucket's hash count fixed at compile time (1 or 2), or 0 to read p.b.
+template <int WORDS, int B>  // WORDS: 32-bit words per stored row (stride / 4)
 __global__ void __launch_bounds__(kPullThreads) k_batch_bloom(BuildParams p) {
     __shared__ uint32_t filt[kPullWarps][32 * WORDS];
     __shared__ uint32_t pre_s[16];
@@ -293,6 +294,8 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_bloom(BuildParams p) {
             const int32_t x_lo = __shfl_sync(0xffffffffu, a, 0), x_hi = __shfl_sync(0xffffffffu, e, 31);
             for (int32_t x0 = x_lo; x0 < x_hi; x0 += 32) {
                 const int32_t x = x0 + (int32_t)lane;
+                // the id load is issued before the row search that it does not depend on
+                const int32_t cx = x < x_hi ? __ldg(p.col + x) : 0;
                 int r = 0;
 #pragma unroll
                 for (int step = 16; step >= 1; step >>= 1) {
@@ -301,11 +304,19 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_bloom(BuildParams p) {
                 }
                 const int32_t idr = __shfl_sync(0xffffffffu, id0, r);
                 if (x < x_hi) {
-                    const uint32_t px = fmix_pre((uint32_t)(__ldg(p.col + x) - idr));
+                    const uint32_t px = fmix_pre((uint32_t)(cx - idr));
                     uint32_t *fr = f + r * WORDS;
-                    for (uint32_t i = 0; i < p.b; ++i) {
-                        const uint32_t q = bit_pos(hash_pre(px, pre_s[i]), p.l);
-                        atomicOr(fr + (q >> 5), 1u << (q & 31u));
+                    if (B > 0) {
+#pragma unroll
+                        for (int i = 0; i < B; ++i) {
+                            const uint32_t q = bit_pos(hash_pre(px, pre_s[i]), p.l);
+                            atomicOr(fr + (q >> 5), 1u << (q & 31u));
+                        }
+                    } else {
+                        for (uint32_t i = 0; i < p.b; ++i) {
+                            const uint32_t q = bit_pos(hash_pre(px, pre_s[i]), p.l);
+                            atomicOr(fr + (q >> 5), 1u << (q & 31u));
+                        }
                     }
                 }
             }
@@ -325,15 +336,23 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_bloom(BuildParams p) {
     }
 }
 
-template <int WORDS>
-cudaError_t run_batch_bloom(const BuildParams &p, cudaStream_t s) {
+template <int WORDS, int B>
+cudaError_t run_batch_bloom_b(const BuildParams &p, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bloom<WORDS>, kPullThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_bloom<WORDS, B>, kPullThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
-    k_batch_bloom<WORDS><<<per_sm * device_info().sm_count, kPullThreads, 0, s>>>(p);
+    k_batch_bloom<WORDS, B><<<per_sm * device_info().sm_count, kPullThreads, 0, s>>>(p);
     note_launch();
     return cudaGetLastError();
+}
+
+// A launch covers graphs of one bucket, which share the hash count p.b.
+template <int WORDS>
+cudaError_t run_batch_bloom(const BuildParams &p, cudaStream_t s) {
+    if (p.b == 1) return run_batch_bloom_b<WORDS, 1>(p, s);
+    if (p.b == 2) return run_batch_bloom_b<WORDS, 2>(p, s);
+    return run_batch_bloom_b<WORDS, 0>(p, s);
 }
 
 // Groups of 32 rows per warp chunk of the build.
