@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_pull(PullParams p) {
             for (int32_t x0 = x_lo; x0 < x_hi; x0 += 32) {
                 const int32_t x = x0 + (int32_t)lane;
                 const bool live = x < x_hi;
+                // the id load is issued before the row search that it does not depend on
+                const int32_t cx = live ? __ldg(p.col + x) : 0;
                 // row of entry x: the number of rows (lanes) ending at or before x
                 int r = 0;
 #pragma unroll
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kPullThreads) k_batch_pull(PullParams p) {
                     if (er <= x) r += step;
                 }
                 const int32_t ur = v0 + r;
-                const int32_t v = live ? __ldg(p.col + x) : ur;
+                const int32_t v = live ? cx : ur;
                 const uint32_t c = and_popc<W>(pull_row<W>(p, ur), pull_row<W>(p, v));
                 unsigned long long V = (v != ur) ? tabV[c] : 0ull;
                 const int32_t gr = __shfl_sync(0xffffffffu, g, r);
