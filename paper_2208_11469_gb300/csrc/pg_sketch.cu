@@ -76,12 +76,15 @@ __device__ __forceinline__ void vertex_params(const BatchMap &bm, int64_t v, uin
 //   Short rows (at most kLaneRow ids, LANE only): each lane builds its own
 //     vertex's filter in a lane-private shared-memory column (word w of lane r
 //     at [w * 32 + r], so every access of lane r is in bank r and needs no
-//     atomic), walking its row id by id, and stores the row as 16-byte vectors.
+//     atomic), walking its row with eight id loads in flight, and stores the
+//     row as 16-byte vectors.
 //   Longer rows: the warp builds one row at a time in a warp-shared filter
 //     with shared atomicOr (32 ids per step, four steps of loads in flight),
 //     fetching the next such row's first ids while hashing the current one.
 //   Hub rows (above hub_threshold): stored empty here and filled by
 //     k_bloom_hub.
+// B: the hash count b fixed at compile time (1 or 2; the seeds' pre-images
+// then live in registers), or 0 to take it per vertex (vertex_params).
 constexpr int32_t kLaneRow = 32;
 
 template <int kMaxWords32, bool LANE, int B>
